@@ -1,0 +1,149 @@
+/*
+ * lw.h -- C ABI of the GB300 Lance-Williams clustering library (liblw.so).
+ *
+ * The library computes an agglomerative hierarchical clustering (a
+ * dendrogram) of n objects from their dissimilarity matrix, smaller meaning
+ * more similar (Yarmish, Listowsky, Dexter, "Distributed Lance-William
+ * Clustering Algorithm": Abstract and Section 1 state the problem, Section 4 the
+ * iteration, Table 1 the coefficients).  Each of the n - 1 merges
+ *   1. finds the minimum remaining distance D(i, j), i < j (Section 4 step 1),
+ *   2. combines i and j into one cluster kept in slot i; slot j is never used
+ *      again (Section 4 step 2; Section 5.3 step 6),
+ *   3. recomputes, for every other live cluster k,
+ *        D(k, i+j) = a_i D(k,i) + a_j D(k,j) + b D(i,j) + g |D(k,i) - D(k,j)|
+ *      with the Table 1 coefficients of the chosen linkage (Section 4 step 3),
+ *   4. outputs the step (i, j, D(i, j)) of the tree (Section 4 step 4).
+ * All n - 1 merges run inside one persistent cooperative CUDA kernel on one
+ * GPU (sm_103a).
+ *
+ * Exact arithmetic contract (bit-exact, ties included):
+ *   - cells are IEEE FP32; every product and sum is rounded to nearest even,
+ *     no fused multiply-add; the four terms are added left to right in the
+ *     order printed above, all four always evaluated;
+ *   - group average: a_i = fl(n_i/(n_i+n_j)), a_j = fl(n_j/(n_i+n_j));
+ *     Ward: T = n_i+n_j+n_k, a_i = fl((n_i+n_k)/T), a_j = fl((n_j+n_k)/T),
+ *     b = -fl(n_k/T), g = 0; single: (0.5, 0.5, 0, -0.5);
+ *     complete: (0.5, 0.5, 0, 0.5) (the form of Section 5.3 step 6);
+ *   - the minimum is the smallest (value, i, j) in lexicographic order, so
+ *     equal distances go to the lowest row i, then the lowest column j.
+ *
+ * Storage (Section 5.1 / 5.2 keep only the upper triangle): the matrix is the packed
+ * row-major strict upper triangle, n(n-1)/2 floats; cell (r, c), r < c, is at
+ * index r*n - r*(r+1)/2 + (c - r - 1) (64-bit arithmetic).
+ *
+ * Errors: every call returns an lw_status; nothing aborts, throws or exits.
+ * Device waits inside kernels are bounded; a wait that runs out reports
+ * LW_ERR_TIMEOUT and leaves the CUDA context usable.
+ */
+#ifndef LW_H
+#define LW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Linkage rows of Table 1 that this library implements. */
+typedef enum {
+    LW_SINGLE = 0,   /* a_i = a_j = 1/2, b = 0, g = -1/2 */
+    LW_COMPLETE = 1, /* a_i = a_j = 1/2, b = 0, g = +1/2 */
+    LW_AVERAGE = 2,  /* a_i = n_i/(n_i+n_j), a_j = n_j/(n_i+n_j), b = g = 0 */
+    LW_WARD = 3      /* a_i = (n_i+n_k)/T, a_j = (n_j+n_k)/T, b = -n_k/T, g = 0 */
+} lw_linkage;
+
+typedef enum {
+    LW_OK = 0,
+    LW_ERR_INVALID_ARG = 1,   /* bad n, linkage, pointer or handle */
+    LW_ERR_INVALID_INPUT = 2, /* a NaN, infinite or negative distance */
+    LW_ERR_OOM = 3,           /* device or host allocation failed */
+    LW_ERR_CUDA = 4,          /* a CUDA runtime call failed (see lw_last_error) */
+    LW_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    LW_ERR_BUSY = 6           /* the context is in use by another call */
+} lw_status;
+
+/* Largest n accepted: cluster sizes stay exact in FP32 and packed indices
+ * fit in 64 bits.  The matrix itself must also fit in device memory. */
+#define LW_MAX_N (1 << 24)
+
+typedef struct lw_ctx lw_ctx;
+
+/*
+ * lw_create -- make a context bound to CUDA device `device`.
+ *   out          receives the handle (host pointer, must not be NULL).
+ *   cuda_stream  a cudaStream_t on that device to issue all work on, or NULL
+ *                for a stream owned by the context.
+ * The context owns its device workspace (row-minimum keys 8n B, cluster
+ * sizes 4n B, per-CTA exchange records, barrier words) and reuses it across
+ * calls; it grows on demand.  Returns LW_ERR_INVALID_ARG for a bad device,
+ * LW_ERR_CUDA if the device cannot be used.
+ */
+lw_status lw_create(lw_ctx **out, int device, void *cuda_stream);
+
+/*
+ * lw_cluster -- cluster one matrix; blocks until the outputs are written.
+ *   dist         packed upper triangle, n(n-1)/2 FP32 cells, row-major.
+ *                If it is a DEVICE pointer it is the working matrix and is
+ *                OVERWRITTEN in place (the paper's update rewrites row and
+ *                column i in place, Section 5.3 step 6): keep a copy if needed.
+ *                If it is a HOST pointer the library copies it to a device
+ *                buffer owned by the context and leaves the host array
+ *                unchanged (pinned memory gives the fastest copy).
+ *   n            number of objects, 1 <= n <= LW_MAX_N.  n == 1: no merges.
+ *   linkage      an lw_linkage value.
+ *   merges_out   int32[2*(n-1)], host or device: step t is
+ *                (merges_out[2t], merges_out[2t+1]) = (i, j), i < j, the
+ *                slots of the two clusters merged; slot i keeps the result.
+ *   heights_out  float[n-1], host or device: heights_out[t] = D(i, j).
+ * Errors: LW_ERR_INVALID_ARG (n out of range, bad linkage, NULL pointer),
+ * LW_ERR_INVALID_INPUT (a NaN/inf/negative cell; outputs unspecified and a
+ * device dist possibly partly rewritten: -0 cells become +0),
+ * LW_ERR_OOM, LW_ERR_CUDA, LW_ERR_TIMEOUT.
+ */
+lw_status lw_cluster(lw_ctx *ctx, float *dist, int64_t n, int linkage,
+                     int32_t *merges_out, float *heights_out);
+
+/*
+ * lw_cluster_async -- as lw_cluster for DEVICE pointers only (dist,
+ * merges_out, heights_out), but returns as soon as the work is queued on the
+ * context's stream.  The status of the run is read by lw_wait.  Returns
+ * LW_ERR_INVALID_ARG if a pointer is not device memory.
+ */
+lw_status lw_cluster_async(lw_ctx *ctx, float *dist, int64_t n, int linkage,
+                           int32_t *merges_out, float *heights_out);
+
+/* lw_wait -- synchronise the context's stream and return the status of the
+ * last queued run (LW_OK, LW_ERR_INVALID_INPUT, LW_ERR_TIMEOUT, ...). */
+lw_status lw_wait(lw_ctx *ctx);
+
+/*
+ * lw_get_stats -- counters of the last completed run (host array of 4):
+ *   [0] rows whose cached minimum was lost and rescanned,
+ *   [1] live cells read by those rescans,
+ *   [2] cells rewritten by the update formula,
+ *   [3] CTAs of the persistent grid.
+ */
+lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4);
+
+/*
+ * lw_set_option -- tuning knobs (0 = automatic):
+ *   LW_OPT_GRID       CTAs of the persistent grid (clamped to co-residency);
+ *   LW_OPT_TIMEOUT_MS bound of every device wait, milliseconds.
+ */
+enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2 };
+lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
+
+/* lw_status_string -- static text for a status code. */
+const char *lw_status_string(lw_status s);
+
+/* lw_last_error -- detail text of the last failure on this context. */
+const char *lw_last_error(lw_ctx *ctx);
+
+/* lw_destroy -- free the context and its device workspace (NULL is a no-op). */
+void lw_destroy(lw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LW_H */
