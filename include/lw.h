@@ -127,11 +127,19 @@ lw_status lw_wait(lw_ctx *ctx);
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4);
 
 /*
- * lw_set_option -- tuning knobs (0 = automatic):
- *   LW_OPT_GRID       CTAs of the persistent grid (clamped to co-residency);
- *   LW_OPT_TIMEOUT_MS bound of every device wait, milliseconds.
+ * lw_set_option -- knobs of the context (value 0 = automatic / default):
+ *   LW_OPT_GRID       CTAs of the persistent grid, 1..SM count (clamped to
+ *                     what fits co-resident);
+ *   LW_OPT_TIMEOUT_MS bound of every device wait in milliseconds (default
+ *                     5000);
+ *   LW_OPT_TEST_SKIP_ARRIVE  failure-detection test hook: CTA `value` of a
+ *                     multi-CTA grid returns before the first grid barrier,
+ *                     so the other CTAs' bounded waits run out and the call
+ *                     reports LW_ERR_TIMEOUT with the context still usable;
+ *                     -1 switches it off (the default).
+ * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
-enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2 };
+enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2, LW_OPT_TEST_SKIP_ARRIVE = 3 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
 /* lw_status_string -- static text for a status code. */

@@ -1,0 +1,472 @@
+// lw_api.cu -- the C ABI of liblw (declared in include/lw.h).
+//
+// Host side only: argument checks, pointer classification, the context's
+// device workspace, copies for host buffers, and the cooperative launch of
+// the persistent merge kernel (lw_merge.cu).  No clustering arithmetic runs
+// on the host.
+
+#include "../../include/lw.h"
+#include "lw_internal.h"
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+struct lw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int grid_opt = 0;
+    long long timeout_ms = 5000;
+    int test_skip_arrive = -1;
+
+    // device workspace
+    void *ws = nullptr;
+    size_t ws_cap = 0;
+    float *dbuf = nullptr;  // device copy of a host matrix
+    size_t dbuf_cap = 0;
+    void *obuf = nullptr;   // device outputs for host output pointers
+    size_t obuf_cap = 0;
+    int *h_status = nullptr;     // pinned [4]
+    long long *h_stats = nullptr;  // pinned [4]
+
+    // views into ws of the last launch
+    int *d_status = nullptr;
+    long long *d_stats = nullptr;
+    bool pending = false;
+    lw_status pending_fail = LW_OK;
+
+    std::atomic<int> busy{0};
+    char err[512] = {0};
+};
+
+namespace {
+
+void set_err(lw_ctx *ctx, const char *fmt, ...)
+{
+    if (!ctx)
+        return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+    va_end(ap);
+}
+
+lw_status cuda_fail(lw_ctx *ctx, cudaError_t e, const char *what)
+{
+    set_err(ctx, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LW_ERR_OOM : LW_ERR_CUDA;
+}
+
+// Is `p` memory the device can address as device memory (cudaMalloc,
+// managed)?  Host pointers (pageable or pinned) return false.
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t rowkey, size, recs, bar, status, stats, total;
+};
+
+Layout layout_for(long long n, int G)
+{
+    Layout L;
+    size_t off = 0;
+    L.rowkey = off; off = align256(off + sizeof(unsigned long long) * (size_t)n);
+    L.size = off;   off = align256(off + sizeof(int) * (size_t)n);
+    L.recs = off;   off = align256(off + sizeof(lw::Rec) * 2 * (size_t)G);
+    L.bar = off;    off = align256(off + 256);
+    L.status = off; off = align256(off + 4 * sizeof(int));
+    L.stats = off;  off = align256(off + 4 * sizeof(long long));
+    L.total = off;
+    return L;
+}
+
+lw_status ensure(lw_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what)
+{
+    if (*cap >= need)
+        return LW_OK;
+    if (*buf) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaStreamSynchronize");
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(ctx, "cudaMalloc(%zu bytes) for %s failed: %s", need, what, cudaGetErrorString(e));
+        return LW_ERR_OOM;
+    }
+    *cap = need;
+    return LW_OK;
+}
+
+struct BusyGuard {
+    lw_ctx *ctx;
+    bool ok;
+    explicit BusyGuard(lw_ctx *c) : ctx(c)
+    {
+        int expected = 0;
+        ok = ctx->busy.compare_exchange_strong(expected, 1);
+    }
+    ~BusyGuard()
+    {
+        if (ok)
+            ctx->busy.store(0);
+    }
+};
+
+int choose_grid(lw_ctx *ctx, long long n)
+{
+    int G = ctx->grid_opt > 0 ? ctx->grid_opt : 0;
+    if (G == 0) {
+        // small matrices: one CTA (no grid barrier); larger: every SM
+        G = n <= 4096 ? 1 : ctx->num_sms;
+    }
+    if (G > ctx->num_sms)
+        G = ctx->num_sms;
+    const long long nb = (n + lw::kRowBlock - 1) / lw::kRowBlock;
+    if (G > nb)
+        G = (int)nb;
+    while (G < ctx->num_sms && !lw::merge_config_ok(n, G, ctx->num_sms))
+        ++G;  // too much shared memory per CTA: spread the rows wider
+    while (G > 1 && !lw::merge_config_ok(n, G, ctx->num_sms))
+        --G;
+    return lw::merge_config_ok(n, G, ctx->num_sms) ? G : 0;
+}
+
+// Queue one run on ctx->stream.  dist/merges/heights are device pointers.
+lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *dmerges,
+                  float *dheights)
+{
+    const int G = choose_grid(ctx, n);
+    if (G <= 0) {
+        set_err(ctx, "n=%lld does not fit a co-resident grid on this device", n);
+        return LW_ERR_INVALID_ARG;
+    }
+    const Layout L = layout_for(n, G);
+    lw_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.total, "workspace");
+    if (s != LW_OK)
+        return s;
+    char *ws = static_cast<char *>(ctx->ws);
+    lw::MergeParams p;
+    p.D = ddist;
+    p.n = n;
+    p.linkage = linkage;
+    p.G = G;
+    p.aligned16 = ((uintptr_t)ddist & 15u) == 0;
+    p.merges = dmerges;
+    p.heights = dheights;
+    p.rowkey_g = reinterpret_cast<unsigned long long *>(ws + L.rowkey);
+    p.size_g = reinterpret_cast<int *>(ws + L.size);
+    p.recs = reinterpret_cast<lw::Rec *>(ws + L.recs);
+    p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
+    p.status = reinterpret_cast<int *>(ws + L.status);
+    p.stats = reinterpret_cast<long long *>(ws + L.stats);
+    p.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
+    p.skip_arrive_cta = (ctx->test_skip_arrive >= 0 && ctx->test_skip_arrive < G && G > 1)
+                            ? ctx->test_skip_arrive : -1;
+    ctx->d_status = p.status;
+    ctx->d_stats = p.stats;
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.rowkey_g, 0xff, sizeof(unsigned long long) * (size_t)n,
+                             ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemsetAsync");
+    // barrier, status and stats words are contiguous from L.bar
+    if ((e = cudaMemsetAsync(ws + L.bar, 0, L.total - L.bar, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemsetAsync");
+    if ((e = lw::launch_merge(p, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaLaunchCooperativeKernel");
+    return LW_OK;
+}
+
+// Copy status/stats back and wait; maps the kernel status word.
+lw_status finish(lw_ctx *ctx)
+{
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemcpyAsync(status)");
+    if ((e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 4 * sizeof(long long),
+                             cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemcpyAsync(stats)");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    const int st = ctx->h_status[0];
+    if (st == lw::kErrInput) {
+        set_err(ctx, "input holds a NaN, infinite or negative distance");
+        return LW_ERR_INVALID_INPUT;
+    }
+    if (st == lw::kErrTimeout) {
+        set_err(ctx, "a device wait exceeded %lld ms (barrier %d)", ctx->timeout_ms,
+                ctx->h_status[1]);
+        return LW_ERR_TIMEOUT;
+    }
+    if (st == lw::kErrInternal) {
+        set_err(ctx, "kernel stopped: the decided pair was out of range (internal error)");
+        return LW_ERR_CUDA;
+    }
+    if (st != 0) {
+        set_err(ctx, "kernel reported status %d", st);
+        return LW_ERR_CUDA;
+    }
+    return LW_OK;
+}
+
+lw_status check_args(lw_ctx *ctx, const float *dist, int64_t n, int linkage, const int32_t *merges,
+                     const float *heights)
+{
+    if (n < 1 || n > LW_MAX_N) {
+        set_err(ctx, "n=%lld out of range [1, %d]", (long long)n, LW_MAX_N);
+        return LW_ERR_INVALID_ARG;
+    }
+    if (linkage < LW_SINGLE || linkage > LW_WARD) {
+        set_err(ctx, "unknown linkage %d", linkage);
+        return LW_ERR_INVALID_ARG;
+    }
+    if (n > 1 && (!dist || !merges || !heights)) {
+        set_err(ctx, "NULL dist, merges_out or heights_out");
+        return LW_ERR_INVALID_ARG;
+    }
+    return LW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lw_status lw_create(lw_ctx **out, int device, void *cuda_stream)
+{
+    if (!out)
+        return LW_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return LW_ERR_CUDA;
+    }
+    if (device < 0 || device >= count)
+        return LW_ERR_INVALID_ARG;
+    lw_ctx *ctx = new (std::nothrow) lw_ctx;
+    if (!ctx)
+        return LW_ERR_OOM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int coop = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (e == cudaSuccess && !coop)
+        e = cudaErrorNotSupported;
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&ctx->h_status, 4 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&ctx->h_stats, 4 * sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lw_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? LW_ERR_OOM : LW_ERR_CUDA;
+    }
+    memset(ctx->h_stats, 0, 4 * sizeof(long long));
+    *out = ctx;
+    return LW_OK;
+}
+
+lw_status lw_cluster(lw_ctx *ctx, float *dist, int64_t n, int linkage, int32_t *merges_out,
+                     float *heights_out)
+{
+    if (!ctx)
+        return LW_ERR_INVALID_ARG;
+    BusyGuard guard(ctx);
+    if (!guard.ok) {
+        set_err(ctx, "context busy");
+        return LW_ERR_BUSY;
+    }
+    lw_status s = check_args(ctx, dist, n, linkage, merges_out, heights_out);
+    if (s != LW_OK)
+        return s;
+    if (n == 1)
+        return LW_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaSetDevice");
+
+    const size_t cells = (size_t)n * (size_t)(n - 1) / 2;
+    float *ddist = dist;
+    if (!is_device_ptr(dist)) {
+        s = ensure(ctx, (void **)&ctx->dbuf, &ctx->dbuf_cap, cells * sizeof(float), "matrix copy");
+        if (s != LW_OK)
+            return s;
+        if ((e = cudaMemcpyAsync(ctx->dbuf, dist, cells * sizeof(float), cudaMemcpyHostToDevice,
+                                 ctx->stream)) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMemcpyAsync(matrix)");
+        ddist = ctx->dbuf;
+    }
+    const bool dev_m = is_device_ptr(merges_out), dev_h = is_device_ptr(heights_out);
+    int32_t *dm = merges_out;
+    float *dh = heights_out;
+    const size_t mbytes = sizeof(int32_t) * 2 * (size_t)(n - 1);
+    const size_t hbytes = sizeof(float) * (size_t)(n - 1);
+    if (!dev_m || !dev_h) {
+        s = ensure(ctx, &ctx->obuf, &ctx->obuf_cap, align256(mbytes) + hbytes, "output buffers");
+        if (s != LW_OK)
+            return s;
+        if (!dev_m)
+            dm = static_cast<int32_t *>(ctx->obuf);
+        if (!dev_h)
+            dh = reinterpret_cast<float *>(static_cast<char *>(ctx->obuf) + align256(mbytes));
+    }
+    s = enqueue(ctx, ddist, n, linkage, dm, dh);
+    if (s != LW_OK)
+        return s;
+    if (!dev_m && (e = cudaMemcpyAsync(merges_out, dm, mbytes, cudaMemcpyDeviceToHost,
+                                       ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemcpyAsync(merges)");
+    if (!dev_h && (e = cudaMemcpyAsync(heights_out, dh, hbytes, cudaMemcpyDeviceToHost,
+                                       ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemcpyAsync(heights)");
+    return finish(ctx);
+}
+
+lw_status lw_cluster_async(lw_ctx *ctx, float *dist, int64_t n, int linkage, int32_t *merges_out,
+                           float *heights_out)
+{
+    if (!ctx)
+        return LW_ERR_INVALID_ARG;
+    BusyGuard guard(ctx);
+    if (!guard.ok) {
+        set_err(ctx, "context busy");
+        return LW_ERR_BUSY;
+    }
+    lw_status s = check_args(ctx, dist, n, linkage, merges_out, heights_out);
+    if (s != LW_OK)
+        return s;
+    ctx->pending = false;
+    ctx->pending_fail = LW_OK;
+    if (n == 1)
+        return LW_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaSetDevice");
+    if (!is_device_ptr(dist) || !is_device_ptr(merges_out) || !is_device_ptr(heights_out)) {
+        set_err(ctx, "lw_cluster_async takes device pointers only");
+        return LW_ERR_INVALID_ARG;
+    }
+    s = enqueue(ctx, dist, n, linkage, merges_out, heights_out);
+    if (s != LW_OK)
+        return s;
+    ctx->pending = true;
+    return LW_OK;
+}
+
+lw_status lw_wait(lw_ctx *ctx)
+{
+    if (!ctx)
+        return LW_ERR_INVALID_ARG;
+    BusyGuard guard(ctx);
+    if (!guard.ok) {
+        set_err(ctx, "context busy");
+        return LW_ERR_BUSY;
+    }
+    if (!ctx->pending) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        return e == cudaSuccess ? LW_OK : cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    ctx->pending = false;
+    return finish(ctx);
+}
+
+lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4)
+{
+    if (!ctx || !stats4)
+        return LW_ERR_INVALID_ARG;
+    for (int q = 0; q < 4; ++q)
+        stats4[q] = ctx->h_stats[q];
+    return LW_OK;
+}
+
+lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
+{
+    if (!ctx)
+        return LW_ERR_INVALID_ARG;
+    switch (option) {
+    case LW_OPT_GRID:
+        if (value < 0 || value > ctx->num_sms)
+            return LW_ERR_INVALID_ARG;
+        ctx->grid_opt = (int)value;
+        return LW_OK;
+    case LW_OPT_TIMEOUT_MS:
+        if (value < 0)
+            return LW_ERR_INVALID_ARG;
+        ctx->timeout_ms = value == 0 ? 5000 : value;
+        return LW_OK;
+    case LW_OPT_TEST_SKIP_ARRIVE:
+        ctx->test_skip_arrive = value < 0 ? -1 : (int)value;
+        return LW_OK;
+    default:
+        return LW_ERR_INVALID_ARG;
+    }
+}
+
+const char *lw_status_string(lw_status s)
+{
+    switch (s) {
+    case LW_OK: return "ok";
+    case LW_ERR_INVALID_ARG: return "invalid argument";
+    case LW_ERR_INVALID_INPUT: return "invalid input (NaN, infinite or negative distance)";
+    case LW_ERR_OOM: return "out of memory";
+    case LW_ERR_CUDA: return "CUDA error";
+    case LW_ERR_TIMEOUT: return "device wait timed out";
+    case LW_ERR_BUSY: return "context busy";
+    }
+    return "unknown status";
+}
+
+const char *lw_last_error(lw_ctx *ctx)
+{
+    return ctx ? ctx->err : "no context";
+}
+
+void lw_destroy(lw_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream)
+        cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->dbuf);
+    cudaFree(ctx->obuf);
+    cudaFreeHost(ctx->h_status);
+    cudaFreeHost(ctx->h_stats);
+    if (ctx->own_stream && ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// lw_internal.h -- declarations shared by the CUDA translation units of liblw.
+// Not part of the public C ABI (include/lw.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lw {
+
+constexpr int kThreads = 512;            // threads per CTA of the merge kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
+constexpr uint64_t kNoKey = ~0ull;
+
+// Status words written by the kernel (values match lw_status).
+enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
+
+// One CTA's contribution to the global minimum of a merge, 32 bytes.
+//   A    = (bits(value) << 32) | row   of the CTA's smallest candidate cell
+//   c    = column of that cell
+//   ikey = (bits(value) << 32) | column  smallest new cell of the survivor
+//          row that this CTA rewrote in the last update
+struct __align__(16) Rec {
+    unsigned long long A;
+    unsigned long long ikey;
+    unsigned int c;
+    unsigned int pad0;
+    unsigned long long pad1;
+};
+
+struct MergeParams {
+    float *D;                      // packed upper triangle, rewritten in place
+    long long n;
+    int linkage;                   // 0 single, 1 complete, 2 average, 3 Ward
+    int G;                         // CTAs in the persistent grid
+    int aligned16;                 // D is 16-byte aligned (128-bit loads allowed)
+    int32_t *merges;               // [2(n-1)] device
+    float *heights;                // [n-1]    device
+    unsigned long long *rowkey_g;  // [n] row-minimum keys built by the initial scan
+    int *size_g;                   // [n] cluster sizes
+    Rec *recs;                     // [2 * G] exchange records (double-buffered)
+    unsigned int *bar;             // grid barrier counter (zero at launch)
+    int *status;                   // [4] status word [0]; wait that gave up [1]
+    long long *stats;              // [4] rescans, rescanned live cells, updated cells, G
+    unsigned long long timeout_ns; // bound of every device wait
+    int skip_arrive_cta;           // failure-detection test: this CTA never reaches the
+                                   // first barrier (-1 = off), so the others' bounded
+                                   // wait runs out and reports LW_ERR_TIMEOUT
+};
+
+// Bytes of dynamic shared memory the merge kernel needs for (n, G).
+size_t merge_smem_bytes(long long n, int G);
+// True if a grid of G CTAs for n objects fits co-resident on the current device.
+bool merge_config_ok(long long n, int G, int num_sms);
+// Launch the persistent kernel cooperatively on `stream`.
+cudaError_t launch_merge(const MergeParams &p, cudaStream_t stream);
+
+}  // namespace lw

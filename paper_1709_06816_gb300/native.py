@@ -1,0 +1,224 @@
+"""ctypes binding of liblw.so (the C ABI in include/lw.h).
+
+Argument marshalling only: every step of the clustering runs in the CUDA
+kernels of liblw.so.  There is no CPU fallback: if the library is missing
+or cannot be loaded, every call raises.
+
+Functions keep the C names (``lw_create``, ``lw_cluster``, ...); the
+``Context`` class wraps them for torch tensors and numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblw.so")
+
+LW_SINGLE, LW_COMPLETE, LW_AVERAGE, LW_WARD = 0, 1, 2, 3
+LINKAGES = {"single": 0, "complete": 1, "average": 2, "ward": 3}
+LW_OPT_GRID, LW_OPT_TIMEOUT_MS = 1, 2
+STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW_ERR_OOM",
+          4: "LW_ERR_CUDA", 5: "LW_ERR_TIMEOUT", 6: "LW_ERR_BUSY"}
+
+# every symbol include/lw.h declares
+EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
+           "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LwError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {detail}")
+
+
+def load(path: str = LIB_PATH):
+    """Load liblw.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run __graft_entry__.build() "
+                               "(the CUDA library is required, there is no fallback)")
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        lib.lw_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+        lib.lw_create.restype = ctypes.c_int
+        for name in ("lw_cluster", "lw_cluster_async"):
+            f = getattr(lib, name)
+            f.argtypes = [vp, vp, i64, ctypes.c_int, vp, vp]
+            f.restype = ctypes.c_int
+        lib.lw_wait.argtypes = [vp]
+        lib.lw_wait.restype = ctypes.c_int
+        lib.lw_get_stats.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.lw_get_stats.restype = ctypes.c_int
+        lib.lw_set_option.argtypes = [vp, ctypes.c_int, i64]
+        lib.lw_set_option.restype = ctypes.c_int
+        lib.lw_status_string.argtypes = [ctypes.c_int]
+        lib.lw_status_string.restype = ctypes.c_char_p
+        lib.lw_last_error.argtypes = [vp]
+        lib.lw_last_error.restype = ctypes.c_char_p
+        lib.lw_destroy.argtypes = [vp]
+        lib.lw_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer {type(x)}")
+
+
+# ---- C-named functions ------------------------------------------------------
+
+def lw_create(device: int = 0, stream=None) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    s = lib.lw_create(ctypes.byref(h), int(device), stream)
+    if s != 0:
+        raise LwError(s, "lw_create")
+    return h.value
+
+
+def lw_cluster(ctx: int, dist, n: int, linkage: int, merges_out, heights_out) -> None:
+    lib = load()
+    s = lib.lw_cluster(ctx, _ptr(dist), int(n), int(linkage), _ptr(merges_out), _ptr(heights_out))
+    if s != 0:
+        raise LwError(s, lib.lw_last_error(ctx).decode())
+
+
+def lw_cluster_async(ctx: int, dist, n: int, linkage: int, merges_out, heights_out) -> None:
+    lib = load()
+    s = lib.lw_cluster_async(ctx, _ptr(dist), int(n), int(linkage), _ptr(merges_out),
+                             _ptr(heights_out))
+    if s != 0:
+        raise LwError(s, lib.lw_last_error(ctx).decode())
+
+
+def lw_wait(ctx: int) -> None:
+    lib = load()
+    s = lib.lw_wait(ctx)
+    if s != 0:
+        raise LwError(s, lib.lw_last_error(ctx).decode())
+
+
+def lw_get_stats(ctx: int) -> dict:
+    lib = load()
+    a = (ctypes.c_int64 * 4)()
+    s = lib.lw_get_stats(ctx, a)
+    if s != 0:
+        raise LwError(s, "lw_get_stats")
+    return {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3]}
+
+
+def lw_set_option(ctx: int, option: int, value: int) -> None:
+    s = load().lw_set_option(ctx, int(option), int(value))
+    if s != 0:
+        raise LwError(s, f"lw_set_option({option}, {value})")
+
+
+def lw_status_string(status: int) -> str:
+    return load().lw_status_string(int(status)).decode()
+
+
+def lw_destroy(ctx: int) -> None:
+    if ctx:
+        load().lw_destroy(ctx)
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class Context:
+    """One lw_ctx on one device; outputs are allocated next to the inputs.
+
+    ``cluster(D, n, linkage)`` takes a flat float32 torch tensor (CUDA or
+    CPU) or numpy array holding the packed upper triangle and returns
+    (merges int32 (n-1, 2), heights float32 (n-1)) of the same kind.  A CUDA
+    ``D`` is overwritten in place (pass ``D.clone()`` to keep it); a host
+    ``D`` is copied by the library and left unchanged.
+    """
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        sp = None
+        if stream is not None:
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.handle = lw_create(device, sp)
+
+    def close(self):
+        if self.handle:
+            lw_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_grid(self, G: int):
+        lw_set_option(self.handle, LW_OPT_GRID, G)
+
+    def set_timeout_ms(self, ms: int):
+        lw_set_option(self.handle, LW_OPT_TIMEOUT_MS, ms)
+
+    def stats(self) -> dict:
+        return lw_get_stats(self.handle)
+
+    def _outputs(self, D, n):
+        m = max(n - 1, 0)
+        if not isinstance(D, np.ndarray):
+            import torch
+            merges = torch.empty((m, 2), dtype=torch.int32, device=D.device)
+            heights = torch.empty(m, dtype=torch.float32, device=D.device)
+        else:
+            merges = np.empty((m, 2), dtype=np.int32)
+            heights = np.empty(m, dtype=np.float32)
+        return merges, heights
+
+    @staticmethod
+    def _check_matrix(D, n):
+        size = D.numel() if hasattr(D, "numel") else D.size
+        dt = str(D.dtype)
+        if "float32" not in dt:
+            raise ValueError("D must be float32")
+        if size != n * (n - 1) // 2:
+            raise ValueError(f"D has {size} cells, expected n(n-1)/2 = {n * (n - 1) // 2}")
+
+    def cluster(self, D, n: int, linkage, merges=None, heights=None):
+        if isinstance(linkage, str):
+            linkage = LINKAGES[linkage]
+        self._check_matrix(D, n)
+        if merges is None or heights is None:
+            merges, heights = self._outputs(D, n)
+        if n <= 1:
+            return merges, heights
+        lw_cluster(self.handle, D, n, linkage, merges, heights)
+        return merges, heights
+
+    def cluster_async(self, D, n: int, linkage, merges, heights):
+        if isinstance(linkage, str):
+            linkage = LINKAGES[linkage]
+        self._check_matrix(D, n)
+        lw_cluster_async(self.handle, D, n, linkage, merges, heights)
+
+    def wait(self):
+        lw_wait(self.handle)

@@ -1,0 +1,229 @@
+"""GPU parity: liblw.so (through its C ABI) against the CPU oracle.
+
+Bar: the merge sequence and the heights are bit-identical (0 ULP, ties
+included) to the oracle on the same seeded inputs.  The GPU path is called
+only through the ctypes binding of include/lw.h.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1709_06816_gb300 import Context, LwError  # noqa: E402
+from paper_1709_06816_gb300 import native  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _bits(a):
+    return np.asarray(a, dtype=np.float32).view(np.uint32)
+
+
+def _gpu(ctx, D_np, n, link, grid=0):
+    ctx.set_grid(grid)
+    dD = torch.from_numpy(np.ascontiguousarray(D_np)).to("cuda")
+    m, h = ctx.cluster(dD, n, link)
+    torch.cuda.synchronize()
+    return m.cpu().numpy(), h.cpu().numpy()
+
+
+def _assert_same(got, want, what=""):
+    gm, gh = got
+    wm, wh = want[0], want[1]
+    if not np.array_equal(gm, wm):
+        t = int(np.argmax((gm != wm).any(axis=1)))
+        raise AssertionError(f"{what}: first differing merge t={t}: gpu {gm[t]} oracle {wm[t]}")
+    if not np.array_equal(_bits(gh), _bits(wh)):
+        t = int(np.argmax(_bits(gh) != _bits(wh)))
+        raise AssertionError(f"{what}: height t={t}: gpu {gh[t]!r} oracle {wh[t]!r}")
+
+
+SMALL_N = [2, 3, 4, 5, 17, 31, 32, 33, 63, 64, 65, 100, 257, 300]
+
+
+@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("kind", ["gmm", "ties"])
+def test_small_single_cta(ctx, link, kind):
+    for s, n in enumerate(SMALL_N):
+        D = synth.small_gmm(n, s) if kind == "gmm" else synth.tie_heavy(n, s)
+        _assert_same(_gpu(ctx, D, n, link, grid=1), oracle.cached(D, n, link), f"n={n}")
+
+
+@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("grid", [2, 3, 7, 32])
+def test_small_multi_cta(ctx, link, grid):
+    """The grid-barrier path at sizes that span several row blocks and a ragged tail."""
+    for s, n in enumerate([33, 65, 100, 257, 300, 1000]):
+        for D in (synth.small_gmm(n, 100 + s), synth.tie_heavy(n, 200 + s, levels=4)):
+            _assert_same(_gpu(ctx, D, n, link, grid=grid), oracle.cached(D, n, link),
+                         f"n={n} grid={grid}")
+
+
+def test_gmm512_complete(ctx):
+    """n = 512 points in R^8 from 8 Gaussians, complete linkage (default grid)."""
+    w = synth.workload("gmm512")
+    D = w.matrix()
+    want = oracle.cached(D, w.n, 1)
+    for grid in (0, 1, 16):
+        _assert_same(_gpu(ctx, D, w.n, 1, grid=grid), want, f"gmm512 grid={grid}")
+
+
+@pytest.mark.parametrize("link", range(4))
+def test_mid_sizes_full_grid(ctx, link):
+    """Several thousand objects over every SM; counters match the oracle's."""
+    for n, seed in [(2048, 1), (4099, 2)]:
+        D = synth.small_gmm(n, seed, dim=16, k=12)
+        want = oracle.cached(D, n, link)
+        _assert_same(_gpu(ctx, D, n, link, grid=torch.cuda.get_device_properties(0).multi_processor_count),
+                     want, f"n={n}")
+        st = ctx.stats()
+        assert st["rescans"] == want[2]["rescans"]
+        assert st["rescan_cells"] == want[2]["rescan_cells"]
+        assert st["updated"] == want[2]["updated"]
+
+
+@pytest.mark.parametrize("link", [0, 1, 2])
+def test_gmm16384_quantized(ctx, link):
+    """n = 16384 in R^64, 32 components, distances on multiples of 1/1024 (ties)."""
+    w = synth.workload("gmm16384q")
+    dD = w.matrix(device="cuda")
+    D = dD.cpu().numpy()
+    want = oracle.cached(D, w.n, link)
+    ctx.set_grid(0)
+    m, h = ctx.cluster(dD, w.n, link)
+    _assert_same((m.cpu().numpy(), h.cpu().numpy()), want, f"gmm16384q link={link}")
+    st = ctx.stats()
+    assert st["rescans"] == want[2]["rescans"] and st["updated"] == want[2]["updated"]
+
+
+@pytest.mark.parametrize("link", [1, 3])
+def test_conformer65536(ctx, link):
+    """n = 65536 conformer-like chains (8.6 GB triangle) in the bench's launch
+    configuration.  The oracle replays the first K merges (a prefix of the
+    same run is the same); the whole GPU run is checked for the structure
+    every dendrogram has (slots retire once, i < j, sizes add up) and, for
+    complete linkage, non-decreasing heights.  Set LW_FULL_ORACLE=1 to
+    compare all 65535 merges."""
+    w = synth.workload("conformer65536")
+    dD = w.matrix(device="cuda")
+    D = dD.cpu().numpy()
+    ctx.set_grid(0)
+    m, h = ctx.cluster(dD, w.n, link)
+    m = m.cpu().numpy()
+    h = h.cpu().numpy()
+    del dD
+    torch.cuda.empty_cache()
+    K = -1 if os.environ.get("LW_FULL_ORACLE") == "1" else 3000
+    want = oracle.cached(D, w.n, link, max_merges=K, inplace=True)
+    k = want[0].shape[0]
+    _assert_same((m[:k], h[:k]), want, f"conformer65536 link={link} first {k} merges")
+    assert (m[:, 0] < m[:, 1]).all()
+    retired = np.zeros(w.n, dtype=bool)
+    for i, j in m:
+        assert not retired[i] and not retired[j]
+        retired[j] = True
+    assert retired.sum() == w.n - 1 and not retired[0]
+    if link == 1:
+        assert (np.diff(h) >= 0).all()
+
+
+def test_host_buffers(ctx):
+    """Host matrix and host outputs: copied by the library, host input untouched."""
+    n = 700
+    D = synth.small_gmm(n, 9)
+    keep = D.copy()
+    ctx.set_grid(0)
+    m, h = ctx.cluster(D, n, 2)
+    assert isinstance(m, np.ndarray)
+    assert np.array_equal(D, keep)
+    _assert_same((m, h), oracle.cached(D, n, 2), "host buffers")
+    # pinned host input
+    P = torch.from_numpy(D).pin_memory()
+    m2, h2 = ctx.cluster(P, n, 2)
+    _assert_same((m2.numpy(), h2.numpy()), oracle.cached(D, n, 2), "pinned")
+
+
+def test_invalid_inputs(ctx):
+    n = 50
+    for grid in (1, 4):
+        ctx.set_grid(grid)
+        for bad in (np.nan, np.inf, -2.0):
+            D = synth.small_gmm(n, 3)
+            D[n] = bad
+            with pytest.raises(LwError) as e:
+                ctx.cluster(torch.from_numpy(D).cuda(), n, 1)
+            assert e.value.status == 2
+        # the context stays usable
+        D = synth.small_gmm(n, 3)
+        _assert_same(_gpu(ctx, D, n, 1, grid=grid), oracle.cached(D, n, 1), "after invalid")
+    # -0 is accepted and behaves as +0
+    D = synth.tie_heavy(n, 5)
+    E = D.copy()
+    E[D == 0] = -0.0
+    _assert_same(_gpu(ctx, E, n, 0, grid=4), oracle.cached(D, n, 0), "-0")
+
+
+def test_invalid_args(ctx):
+    h = ctx.handle
+    m = torch.empty((4, 2), dtype=torch.int32, device="cuda")
+    hh = torch.empty(4, dtype=torch.float32, device="cuda")
+    D = torch.zeros(10, device="cuda")
+    with pytest.raises(LwError) as e:
+        native.lw_cluster(h, D, 0, 1, m, hh)
+    assert e.value.status == 1
+    with pytest.raises(LwError) as e:
+        native.lw_cluster(h, D, 5, 9, m, hh)
+    assert e.value.status == 1
+    with pytest.raises(LwError) as e:
+        native.lw_cluster(h, 0, 5, 1, m, hh)
+    assert e.value.status == 1
+    native.lw_cluster(h, 0, 1, 1, 0, 0)  # n = 1: nothing to do
+    assert native.lw_status_string(5) == "device wait timed out"
+
+
+def test_bounded_wait_reports_timeout(ctx):
+    """A CTA that never reaches the barrier: the others give up after the
+    bound, the call returns LW_ERR_TIMEOUT and the context keeps working."""
+    n = 300
+    D = synth.small_gmm(n, 4)
+    ctx.set_timeout_ms(200)
+    native.lw_set_option(ctx.handle, 3, 2)
+    try:
+        with pytest.raises(LwError) as e:
+            _gpu(ctx, D, n, 1, grid=4)
+        assert e.value.status == 5
+    finally:
+        native.lw_set_option(ctx.handle, 3, -1)
+        ctx.set_timeout_ms(0)
+    _assert_same(_gpu(ctx, D, n, 1, grid=4), oracle.cached(D, n, 1), "after timeout")
+
+
+def test_async_and_stream(ctx):
+    n = 1500
+    D = synth.small_gmm(n, 12)
+    s = torch.cuda.Stream()
+    c2 = Context(0, stream=s)
+    try:
+        dD = torch.from_numpy(D).cuda()
+        m = torch.empty((n - 1, 2), dtype=torch.int32, device="cuda")
+        h = torch.empty(n - 1, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        c2.cluster_async(dD, n, 3, m, h)
+        c2.wait()
+        _assert_same((m.cpu().numpy(), h.cpu().numpy()), oracle.cached(D, n, 3), "async")
+    finally:
+        c2.close()
