@@ -325,7 +325,7 @@ def run_reference(args, world, rank, local):
     import oracle
     import synth
 
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     n = w.n
     if torch.cuda.is_available():
         D_host = w.matrix(device=f"cuda:{local}").cpu().numpy()
@@ -350,7 +350,7 @@ def run_reference(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "linkage": "complete",
+        "config": {"workload": args.workload, "n": n, "linkage": "complete",
                    "l2": "inputs larger than L2 (8.59 GB packed triangle)",
                    "parallelism": "host cores (OpenMP)"},
         "impl": "reference",
