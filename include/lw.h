@@ -142,6 +142,37 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4);
 enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2, LW_OPT_TEST_SKIP_ARRIVE = 3 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
+/*
+ * lw_cluster_noalloc -- lw_cluster for callers that must not allocate.
+ * (Not a step of the paper: the paper has no counterpart; this is a service
+ * of the library.)
+ *
+ * For code that cannot call cudaMalloc/cudaFree when it clusters -- inside a
+ * memory pool or arena that owns every allocation, inside a host
+ * application's plug-in, or in a loop that must never enter the allocator.
+ * It needs no lw_ctx and allocates nothing, host or device: the kernel's
+ * scratch (row keys, sizes, exchange records, barrier words) is a fixed
+ * file-scope device array of 256 KB in liblw.so, created when the library is
+ * loaded on a device and held by every device that loads it until the
+ * process exits.
+ *   dist, merges_out, heights_out  DEVICE pointers as for lw_cluster (dist is
+ *                overwritten in place); n <= LW_NOALLOC_MAX_N.
+ *   cuda_stream  stream to run on (NULL: the legacy default stream); the call
+ *                blocks until the run is finished.
+ * The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls share the one scratch array,
+ * which keeps the last call's contents (each call clears what must start
+ * zeroed), so calls that overlap on the GPU -- from several host threads or
+ * streams at once -- race and must be serialised by the caller.
+ * Errors: LW_ERR_INVALID_ARG for n > LW_NOALLOC_MAX_N, a bad linkage or a
+ * pointer that is not device memory; LW_ERR_INVALID_INPUT, LW_ERR_TIMEOUT
+ * and LW_ERR_CUDA as for lw_cluster.
+ */
+#define LW_NOALLOC_MAX_N 16384
+lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int32_t *merges_out,
+                             float *heights_out, void *cuda_stream);
+
 /* lw_status_string -- static text for a status code. */
 const char *lw_status_string(lw_status s);
 

@@ -48,6 +48,28 @@ struct MergeParams {
                                    // wait runs out and reports LW_ERR_TIMEOUT
 };
 
+// Byte offsets of the merge kernel's global scratch inside one workspace
+// block (every part 256-byte aligned).  The barrier, status and stats words
+// are contiguous from `bar` to `total` so one memset clears them.
+struct WorkspaceLayout {
+    size_t rowkey, size, recs, bar, status, stats, total;
+};
+
+inline WorkspaceLayout workspace_layout(long long n, int G)
+{
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    WorkspaceLayout L;
+    size_t off = 0;
+    L.rowkey = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
+    L.size = off;   off = up(off + sizeof(int) * (size_t)n);
+    L.recs = off;   off = up(off + sizeof(Rec) * 2 * (size_t)G);
+    L.bar = off;    off = up(off + 256);
+    L.status = off; off = up(off + 4 * sizeof(int));
+    L.stats = off;  off = up(off + 4 * sizeof(long long));
+    L.total = off;
+    return L;
+}
+
 // Bytes of dynamic shared memory the merge kernel needs for (n, G).
 size_t merge_smem_bytes(long long n, int G);
 // True if a grid of G CTAs for n objects fits co-resident on the current device.

@@ -26,7 +26,9 @@ STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW
 
 # every symbol include/lw.h declares
 EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
-           "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy")
+           "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy",
+           "lw_cluster_noalloc")
+LW_NOALLOC_MAX_N = 16384
 
 _lib = None
 _lock = threading.Lock()
@@ -68,6 +70,8 @@ def load(path: str = LIB_PATH):
         lib.lw_last_error.restype = ctypes.c_char_p
         lib.lw_destroy.argtypes = [vp]
         lib.lw_destroy.restype = None
+        lib.lw_cluster_noalloc.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
+        lib.lw_cluster_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -133,6 +137,19 @@ def lw_set_option(ctx: int, option: int, value: int) -> None:
     s = load().lw_set_option(ctx, int(option), int(value))
     if s != 0:
         raise LwError(s, f"lw_set_option({option}, {value})")
+
+
+def lw_cluster_noalloc(dist, n: int, linkage: int, merges_out, heights_out, stream=None) -> None:
+    """Clustering for callers that cannot allocate: device buffers only,
+    scratch in the library's fixed device array (n <= LW_NOALLOC_MAX_N)."""
+    lib = load()
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    s = lib.lw_cluster_noalloc(_ptr(dist), int(n), int(linkage), _ptr(merges_out),
+                               _ptr(heights_out), sp)
+    if s != 0:
+        raise LwError(s, "lw_cluster_noalloc")
 
 
 def lw_status_string(status: int) -> str:
