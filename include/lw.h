@@ -118,13 +118,17 @@ lw_status lw_cluster_async(lw_ctx *ctx, float *dist, int64_t n, int linkage,
 lw_status lw_wait(lw_ctx *ctx);
 
 /*
- * lw_get_stats -- counters of the last completed run (host array of 4):
- *   [0] rows whose cached minimum was lost and rescanned,
+ * lw_get_stats -- counters of the last completed run, written to the host
+ * array `stats` (first `count` entries; entries past the last counter are 0):
+ *   [0] rows rescanned at once by their owner (cache emptied),
  *   [1] live cells read by those rescans,
- *   [2] cells rewritten by the update formula,
- *   [3] CTAs of the persistent grid.
+ *   [2] cells rewritten by the update formula (sum over merges of m_t - 2),
+ *   [3] CTAs of the persistent grid,
+ *   [4] row refills served by all CTAs together,
+ *   [5] live cells read by those refills,
+ *   [6] refills installed by the rows' owners.
  */
-lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4);
+lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 
 /*
  * lw_set_option -- knobs of the context (value 0 = automatic / default):
@@ -151,8 +155,8 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
  * memory pool or arena that owns every allocation, inside a host
  * application's plug-in, or in a loop that must never enter the allocator.
  * It needs no lw_ctx and allocates nothing, host or device: the kernel's
- * scratch (row keys, sizes, exchange records, barrier words) is a fixed
- * file-scope device array of 256 KB in liblw.so, created when the library is
+ * scratch (cluster sizes, exchange records, barrier words) is a fixed
+ * file-scope device array of 512 KB in liblw.so, created when the library is
  * loaded on a device and held by every device that loads it until the
  * process exits.
  *   dist, merges_out, heights_out  DEVICE pointers as for lw_cluster (dist is

@@ -30,8 +30,8 @@ struct lw_ctx {
     size_t dbuf_cap = 0;
     void *obuf = nullptr;   // device outputs for host output pointers
     size_t obuf_cap = 0;
-    int *h_status = nullptr;     // pinned [4]
-    long long *h_stats = nullptr;  // pinned [4]
+    int *h_status = nullptr;       // pinned [4]
+    long long *h_stats = nullptr;  // pinned [lw::kStats]
 
     // views into ws of the last launch
     int *d_status = nullptr;
@@ -74,24 +74,6 @@ bool is_device_ptr(const void *p)
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-struct Layout {
-    size_t rowkey, size, recs, bar, status, stats, total;
-};
-
-Layout layout_for(long long n, int G)
-{
-    Layout L;
-    size_t off = 0;
-    L.rowkey = off; off = align256(off + sizeof(unsigned long long) * (size_t)n);
-    L.size = off;   off = align256(off + sizeof(int) * (size_t)n);
-    L.recs = off;   off = align256(off + sizeof(lw::Rec) * 2 * (size_t)G);
-    L.bar = off;    off = align256(off + 256);
-    L.status = off; off = align256(off + 4 * sizeof(int));
-    L.stats = off;  off = align256(off + 4 * sizeof(long long));
-    L.total = off;
-    return L;
-}
 
 lw_status ensure(lw_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what)
 {
@@ -158,7 +140,7 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
         set_err(ctx, "n=%lld does not fit a co-resident grid on this device", n);
         return LW_ERR_INVALID_ARG;
     }
-    const Layout L = layout_for(n, G);
+    const lw::WorkspaceLayout L = lw::workspace_layout(n, G);
     lw_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.total, "workspace");
     if (s != LW_OK)
         return s;
@@ -171,9 +153,12 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     p.aligned16 = ((uintptr_t)ddist & 15u) == 0;
     p.merges = dmerges;
     p.heights = dheights;
-    p.rowkey_g = reinterpret_cast<unsigned long long *>(ws + L.rowkey);
     p.size_g = reinterpret_cast<int *>(ws + L.size);
-    p.recs = reinterpret_cast<lw::Rec *>(ws + L.recs);
+    p.cand = reinterpret_cast<lw::Rec *>(ws + L.cand);
+    p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
+    p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
+    p.req = reinterpret_cast<int *>(ws + L.req);
+    p.nreq = reinterpret_cast<int *>(ws + L.nreq);
     p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
     p.status = reinterpret_cast<int *>(ws + L.status);
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
@@ -184,11 +169,8 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     ctx->d_stats = p.stats;
 
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p.rowkey_g, 0xff, sizeof(unsigned long long) * (size_t)n,
-                             ctx->stream)) != cudaSuccess)
-        return cuda_fail(ctx, e, "cudaMemsetAsync");
-    // barrier, status and stats words are contiguous from L.bar
-    if ((e = cudaMemsetAsync(ws + L.bar, 0, L.total - L.bar, ctx->stream)) != cudaSuccess)
+    // request counts, barrier, status and stats words are contiguous
+    if ((e = cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
     if ((e = lw::launch_merge(p, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaLaunchCooperativeKernel");
@@ -202,7 +184,7 @@ lw_status finish(lw_ctx *ctx)
     if ((e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemcpyAsync(status)");
-    if ((e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 4 * sizeof(long long),
+    if ((e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, lw::kStats * sizeof(long long),
                              cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemcpyAsync(stats)");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
@@ -285,13 +267,13 @@ lw_status lw_create(lw_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&ctx->h_status, 4 * sizeof(int));
     if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&ctx->h_stats, 4 * sizeof(long long));
+        e = cudaMallocHost((void **)&ctx->h_stats, lw::kStats * sizeof(long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         lw_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? LW_ERR_OOM : LW_ERR_CUDA;
     }
-    memset(ctx->h_stats, 0, 4 * sizeof(long long));
+    memset(ctx->h_stats, 0, lw::kStats * sizeof(long long));
     *out = ctx;
     return LW_OK;
 }
@@ -400,12 +382,12 @@ lw_status lw_wait(lw_ctx *ctx)
     return finish(ctx);
 }
 
-lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats4)
+lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count)
 {
-    if (!ctx || !stats4)
+    if (!ctx || !stats || count < 0)
         return LW_ERR_INVALID_ARG;
-    for (int q = 0; q < 4; ++q)
-        stats4[q] = ctx->h_stats[q];
+    for (int q = 0; q < count; ++q)
+        stats[q] = q < lw::kStats ? ctx->h_stats[q] : 0;
     return LW_OK;
 }
 

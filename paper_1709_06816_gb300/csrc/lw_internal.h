@@ -10,22 +10,23 @@ namespace lw {
 constexpr int kThreads = 512;            // threads per CTA of the merge kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
+constexpr int kCacheKeys = 4;            // smallest keys cached per row
+constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
+constexpr int kMaxReq = 32;              // refill requests served per merge
+constexpr int kStats = 8;
 constexpr uint64_t kNoKey = ~0ull;
 
 // Status words written by the kernel (values match lw_status).
 enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
 
-// One CTA's contribution to the global minimum of a merge, 32 bytes.
-//   A    = (bits(value) << 32) | row   of the CTA's smallest candidate cell
-//   c    = column of that cell
-//   ikey = (bits(value) << 32) | column  smallest new cell of the survivor
-//          row that this CTA rewrote in the last update
+// One CTA's candidate for the global minimum of a merge, 32 bytes:
+//   A = (bits(value) << 32) | row,  c = column  of the CTA's smallest cell.
 struct __align__(16) Rec {
     unsigned long long A;
-    unsigned long long ikey;
+    unsigned long long pad0;
     unsigned int c;
-    unsigned int pad0;
-    unsigned long long pad1;
+    unsigned int pad1;
+    unsigned long long pad2;
 };
 
 struct MergeParams {
@@ -36,12 +37,15 @@ struct MergeParams {
     int aligned16;                 // D is 16-byte aligned (128-bit loads allowed)
     int32_t *merges;               // [2(n-1)] device
     float *heights;                // [n-1]    device
-    unsigned long long *rowkey_g;  // [n] row-minimum keys built by the initial scan
     int *size_g;                   // [n] cluster sizes
-    Rec *recs;                     // [2 * G] exchange records (double-buffered)
+    Rec *cand;                     // [2][G] candidates (double-buffered by merge parity)
+    unsigned long long *islice;    // [2][G][kCacheKeys] survivor-row partial top-K
+    unsigned long long *parts;     // [2][G][kMaxReq][kCacheKeys] refill partial top-K
+    int *req;                      // [3][kMaxReq] rows asking for a refill
+    int *nreq;                     // [3] request counts (zero at launch)
     unsigned int *bar;             // grid barrier counter (zero at launch)
-    int *status;                   // [4] status word [0]; wait that gave up [1]
-    long long *stats;              // [4] rescans, rescanned live cells, updated cells, G
+    int *status;                   // [4] status word [0]; barrier that gave up [1]
+    long long *stats;              // [kStats] counters, see lw_get_stats
     unsigned long long timeout_ns; // bound of every device wait
     int skip_arrive_cta;           // failure-detection test: this CTA never reaches the
                                    // first barrier (-1 = off), so the others' bounded
@@ -49,10 +53,10 @@ struct MergeParams {
 };
 
 // Byte offsets of the merge kernel's global scratch inside one workspace
-// block (every part 256-byte aligned).  The barrier, status and stats words
-// are contiguous from `bar` to `total` so one memset clears them.
+// block (every part 256-byte aligned).  The words from `zero` to `total`
+// (request counts, barrier, status, stats) must be zero at launch.
 struct WorkspaceLayout {
-    size_t rowkey, size, recs, bar, status, stats, total;
+    size_t size, cand, islice, parts, req, zero, nreq, bar, status, stats, total;
 };
 
 inline WorkspaceLayout workspace_layout(long long n, int G)
@@ -60,12 +64,16 @@ inline WorkspaceLayout workspace_layout(long long n, int G)
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     WorkspaceLayout L;
     size_t off = 0;
-    L.rowkey = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
     L.size = off;   off = up(off + sizeof(int) * (size_t)n);
-    L.recs = off;   off = up(off + sizeof(Rec) * 2 * (size_t)G);
+    L.cand = off;   off = up(off + sizeof(Rec) * 2 * (size_t)G);
+    L.islice = off; off = up(off + 8 * kCacheKeys * 2 * (size_t)G);
+    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 2 * (size_t)G);
+    L.req = off;    off = up(off + sizeof(int) * 3 * kMaxReq);
+    L.zero = off;
+    L.nreq = off;   off = up(off + sizeof(int) * 3);
     L.bar = off;    off = up(off + 256);
     L.status = off; off = up(off + 4 * sizeof(int));
-    L.stats = off;  off = up(off + 4 * sizeof(long long));
+    L.stats = off;  off = up(off + kStats * sizeof(long long));
     L.total = off;
     return L;
 }

@@ -5,25 +5,35 @@
 // spreads the packed upper triangle over MPI processes and exchanges local
 // minima and (i, j, distance) triples by messages (Section 5.3 steps 1-6b); on
 // one GB300 the whole triangle sits in HBM, so the "processors" become CTAs,
-// the broadcast of local minima becomes a 32-byte record per CTA read after
-// one grid barrier, and the triple exchange disappears: every CTA addresses
-// row and column i and j directly.
+// the broadcast of local minima becomes one 32-byte record per CTA read after
+// a grid barrier, and the triple exchange disappears: every CTA addresses row
+// and column i and j directly.
 //
 // Work split.  Rows are dealt to CTAs in blocks of 32 consecutive rows,
-// round-robin (block q -> CTA q mod G).  The CTA that owns row k
-//   - keeps row k's cached minimum key (smallest (value, column) over live
-//     columns c > k) in shared memory,
-//   - applies the update of Section 4 step 3 for k at every merge: reads
-//     D(k,i), D(k,j), writes D(k,i+j) into D(k,i),
-//   - repairs row k's cached minimum, rescanning row k when the cached
-//     minimum pointed at i or j and the new value is larger.
+// round-robin (block q -> CTA q mod G); a CTA "owns" those rows and, by the
+// same map, those columns.  The owner of row k
+//   - keeps, in shared memory, the kCacheKeys smallest keys of row k
+//     (key = (value bits << 32) | column, over live columns c > k) and a bound
+//     B: every live cell of the row outside the cache has a key above B;
+//   - applies the update of Section 4 step 3 for k at every merge: reads D(k,i),
+//     D(k,j), writes D(k,i+j) into D(k,i), and maintains row k's cache
+//     (drops columns i and j, inserts the new cell (k,i) when it is <= B).
+// The row minimum is exact while the cache is not empty.  A row whose cache
+// runs low asks for a refill; in the NEXT merge every CTA scans its own
+// columns of that row and publishes a partial top-K list, and one merge later
+// the owner merges the lists (applying the one update that happened in
+// between).  So no CTA scans a long row alone on the critical path; only a
+// row whose cache empties before its refill lands is rescanned at once by
+// its owner.
+//
 // The survivor row i is rewritten by every CTA (one cell per owned k > i);
-// each CTA folds its part of row i into the candidate it publishes, and the
-// owner of i reassembles row i's minimum from all records after the barrier.
+// each CTA folds its part of row i into its candidate and publishes its
+// partial top-K of row i, and the owner of i merges those lists after the
+// barrier.
 //
 // One grid barrier per merge:
-//   [barrier] read G records -> global minimum (value, i, j) -> emit step
-//   -> update + repairs + rescans -> publish record -> [barrier]
+//   [barrier] read G candidates -> global minimum (value, i, j) -> emit step
+//   -> update + cache upkeep + refill scans -> publish records -> [barrier]
 //
 // Exact arithmetic: every product and sum of the update uses __fmul_rn /
 // __fadd_rn / __fsub_rn (never contracted into FMA), the coefficient
@@ -33,12 +43,11 @@
 // (bits << 32 | index) gives the lexicographic order.
 //
 // Memory model.  L1 is not coherent across SMs, so every load of data that
-// another CTA may have written (matrix cells, keys, records, sizes) is an
-// L2 load (ld.global.cg) and every store bypasses L1 (st.global.cg).  The
-// barrier is the cooperative-groups pattern: __syncthreads, one thread
-// fences, arrives with a release add and spins with acquire loads.  Each spin
-// is bounded by a wall-clock limit after which the kernel records
-// LW_ERR_TIMEOUT and returns.
+// another CTA may have written (matrix cells, records, sizes) is an L2 load
+// (ld.global.cg) and every store bypasses L1 (st.global.cg).  The barrier is
+// the cooperative-groups pattern: __syncthreads, one thread fences, arrives
+// with a release add and spins with acquire loads.  Each spin is bounded by a
+// wall-clock limit after which the kernel records LW_ERR_TIMEOUT and returns.
 
 #include "lw_internal.h"
 
@@ -48,6 +57,8 @@ namespace lw {
 namespace {
 
 typedef unsigned long long u64;
+constexpr int K = kCacheKeys;
+static_assert(K == 4, "the cache upkeep below sorts four keys with a fixed network");
 
 __device__ __forceinline__ long long tri_off(long long r, long long n)
 {
@@ -90,21 +101,80 @@ __device__ __forceinline__ u64 global_ns()
     return t;
 }
 
-// Candidate of the global minimum plus the survivor-row partial minimum.
+// ---------------------------------------------------------------------------
+// sorted key lists (ascending, padded with kNoKey)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cswap(u64 &a, u64 &b)
+{
+    const u64 lo = a < b ? a : b;
+    b = a < b ? b : a;
+    a = lo;
+}
+
+// Insert x into the K smallest: a compare-swap pass; the largest falls off.
+__device__ __forceinline__ void list_insert(u64 (&L)[K], u64 x)
+{
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        cswap(L[q], x);
+}
+
+// Sort four keys (removed entries are kNoKey and sink to the end).
+__device__ __forceinline__ void sort4(u64 (&L)[K])
+{
+    cswap(L[0], L[1]);
+    cswap(L[2], L[3]);
+    cswap(L[0], L[2]);
+    cswap(L[1], L[3]);
+    cswap(L[1], L[2]);
+}
+
+__device__ __forceinline__ int list_count(const u64 (&L)[K])
+{
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        c += L[q] != kNoKey;
+    return c;
+}
+
+__device__ __forceinline__ u64 warp_u64_min(u64 v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const u64 o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+// K smallest keys over the lists of a warp (keys are distinct or kNoKey).
+__device__ __forceinline__ void warp_topk(u64 (&L)[K], u64 (&out)[K])
+{
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const u64 m = warp_u64_min(L[0]);
+        out[q] = m;
+        if (m != kNoKey && L[0] == m) {
+#pragma unroll
+            for (int s = 0; s + 1 < K; ++s)
+                L[s] = L[s + 1];
+            L[K - 1] = kNoKey;
+        }
+    }
+}
+
+// Candidate of the global minimum: (value, row) and column.
 struct Cand {
     u64 A;       // (bits(v) << 32) | row
     unsigned c;  // column
-    u64 K;       // (bits(v) << 32) | column, survivor row partial
 };
 
 __device__ __forceinline__ void cand_min(Cand &x, const Cand &y)
 {
-    if (y.A < x.A || (y.A == x.A && y.c < x.c)) {
-        x.A = y.A;
-        x.c = y.c;
-    }
-    if (y.K < x.K)
-        x.K = y.K;
+    if (y.A < x.A || (y.A == x.A && y.c < x.c))
+        x = y;
 }
 
 __device__ __forceinline__ Cand warp_cand_min(Cand v)
@@ -114,27 +184,21 @@ __device__ __forceinline__ Cand warp_cand_min(Cand v)
         Cand o;
         o.A = __shfl_xor_sync(0xffffffffu, v.A, off);
         o.c = __shfl_xor_sync(0xffffffffu, v.c, off);
-        o.K = __shfl_xor_sync(0xffffffffu, v.K, off);
         cand_min(v, o);
-    }
-    return v;
-}
-
-__device__ __forceinline__ u64 warp_u64_min(u64 v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        u64 o = __shfl_xor_sync(0xffffffffu, v, off);
-        v = o < v ? o : v;
     }
     return v;
 }
 
 struct Shared {
     Cand red[kWarps + 1];
-    u64 kred[kWarps + 1];
+    u64 tk[kWarps][K];
+    u64 tko[K];
     int flag;
-    int nresc;
+    int nresc;               // rows to rescan at once this merge
+    int nexec;               // refill rows served this merge
+    int exec_row[kMaxReq];
+    int ninst;               // refills to install at the start of the next merge
+    int inst_slot[kMaxReq];  // owned slots of those rows
 };
 
 __device__ Cand block_cand_min(Cand v, Shared &sh)
@@ -145,7 +209,7 @@ __device__ Cand block_cand_min(Cand v, Shared &sh)
         sh.red[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        Cand w = {kNoKey, 0xffffffffu, kNoKey};
+        Cand w = {kNoKey, 0xffffffffu};
         if (lane < kWarps)
             w = sh.red[lane];
         w = warp_cand_min(w);
@@ -156,21 +220,31 @@ __device__ Cand block_cand_min(Cand v, Shared &sh)
     return sh.red[kWarps];
 }
 
-__device__ u64 block_u64_min(u64 v, Shared &sh)
+// K smallest keys over every thread's list; result in sh.tko (all threads).
+__device__ void block_topk(u64 (&L)[K], Shared &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_u64_min(v);
-    if (lane == 0)
-        sh.kred[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        u64 w = lane < kWarps ? sh.kred[lane] : kNoKey;
-        w = warp_u64_min(w);
-        if (lane == 0)
-            sh.kred[kWarps] = w;
+    u64 w[K];
+    warp_topk(L, w);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            sh.tk[warp][q] = w[q];
     }
     __syncthreads();
-    return sh.kred[kWarps];
+    if (warp == 0) {
+        u64 M[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            M[q] = lane < kWarps ? sh.tk[lane][q] : kNoKey;
+        warp_topk(M, w);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                sh.tko[q] = w[q];
+        }
+    }
+    __syncthreads();
 }
 
 // Grid-wide barrier with a bounded wait.  Returns false when the run must
@@ -208,162 +282,113 @@ __device__ bool grid_sync(const MergeParams &p, unsigned &epoch, Shared &sh)
     return sh.flag == 0;
 }
 
-// Row r of the packed triangle that holds flat index q (0 <= q < n(n-1)/2).
-__device__ long long row_of_flat(long long q, long long n)
+// Live-column test against the CTA's copy of the liveness bitmap.
+__device__ __forceinline__ bool live(const unsigned *bitmap, long long c)
 {
-    const double b = 2.0 * (double)n - 1.0;
-    double disc = b * b - 8.0 * (double)q;
-    if (disc < 0.0)
-        disc = 0.0;
-    long long r = (long long)((b - sqrt(disc)) * 0.5);
-    if (r < 0)
-        r = 0;
-    if (r > n - 2)
-        r = n - 2;
-    while (r < n - 2 && tri_off(r + 1, n) <= q)
-        ++r;
-    while (r > 0 && tri_off(r, n) > q)
-        --r;
-    return r;
+    return (bitmap[c >> 5] >> (c & 31)) & 1u;
 }
 
-// Checks one input cell (finite and >= 0), canonicalises -0, returns its key.
-__device__ __forceinline__ u64 init_cell(float v, long long q, unsigned c, const MergeParams &p,
-                                         int &bad)
+// Adds one input cell to a per-lane list during the initial scan: checks it
+// (finite and >= 0), rewrites -0 as +0 in memory, and keeps the K smallest.
+__device__ __forceinline__ void init_cell(float v, long long q, unsigned c, const MergeParams &p,
+                                          u64 (&L)[K], int &bad)
 {
-    const unsigned bits = __float_as_uint(v);
-    if (!(v >= 0.0f) || bits == 0x7f800000u) {
-        bad = 1;
-        return kNoKey;
+    unsigned u = __float_as_uint(v);
+    if (u > 0x7f7fffffu) {
+        if (u == 0x80000000u) {
+            __stcg(p.D + q, 0.0f);
+            u = 0u;
+        } else {
+            bad = 1;
+            return;
+        }
     }
-    if (bits == 0x80000000u) {
-        __stcg(p.D + q, 0.0f);
-        return (u64)c;
-    }
-    return ((u64)bits << 32) | (u64)c;
-}
-
-// Phase 0: validate every cell and build the row-minimum keys.  The packed
-// triangle is split into equal, 512-cell-aligned chunks, one per warp of the
-// grid (the paper's even split of the non-blank cells, Section 5.2); a warp walks its
-// chunk with 128-bit loads and flushes each row's minimum with atomicMin.
-__device__ void initial_scan(const MergeParams &p)
-{
-    const long long n = p.n;
-    const long long N = n * (n - 1) / 2;
-    const int lane = threadIdx.x & 31;
-    const long long W = (long long)p.G * kWarps;
-    const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    long long S = (N + W - 1) / W;
-    S = (S + 511) & ~511LL;
-    const long long lo = w * S;
-    const long long hi = lo + S < N ? lo + S : N;
-    if (lo >= hi)
+    // cells above the list's largest value cannot enter it
+    if (u > (unsigned)(L[K - 1] >> 32))
         return;
-    long long r = row_of_flat(lo, n);
-    long long rs = tri_off(r, n), re = tri_off(r + 1, n);
-    u64 run = kNoKey;
-    int bad = 0;
-    for (long long s = lo; s < hi; s += 512) {
-        float v[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const long long q = s + 128 * u + 4 * lane;
-            if (p.aligned16 && q + 4 <= hi) {
-                const float4 x = __ldcg(reinterpret_cast<const float4 *>(p.D + q));
-                v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    v[u][e] = q + e < hi ? __ldcg(p.D + q + e) : 0.0f;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const long long q0 = s + 128 * u;
-            if (q0 >= hi)
-                break;
-            const long long span_end = q0 + 128 < hi ? q0 + 128 : hi;
-            while (true) {
-                const long long seg_end = re < span_end ? re : span_end;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const long long q = q0 + 4 * lane + e;
-                    if (q >= rs && q < seg_end) {
-                        const u64 k = init_cell(v[u][e], q, (unsigned)(q - rs + r + 1), p, bad);
-                        run = k < run ? k : run;
-                    }
-                }
-                if (seg_end == re) {
-                    const u64 m = warp_u64_min(run);
-                    if (lane == 0 && m != kNoKey)
-                        atomicMin(p.rowkey_g + r, m);
-                    run = kNoKey;
-                    ++r;
-                    rs = re;
-                    re = tri_off(r + 1, n);
-                    if (rs >= span_end)
-                        break;
-                } else {
-                    break;
-                }
-            }
-        }
-    }
-    const u64 m = warp_u64_min(run);
-    if (lane == 0 && m != kNoKey)
-        atomicMin(p.rowkey_g + r, m);
-    if (bad)
-        atomicCAS(p.status, 0, kErrInput);
+    list_insert(L, ((u64)u << 32) | (u64)c);
 }
 
-// Minimum key over the live columns c > k of row k, computed by the whole
-// CTA; adds the number of live cells read to `live`.
-__device__ u64 rescan_row(const MergeParams &p, long long k, const unsigned *bitmap, Shared &sh,
-                          long long &live)
+// K smallest keys of row r (all columns are live at launch), computed by one
+// warp that also validates every cell of the row.
+__device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], int &bad)
 {
     const long long n = p.n;
-    const long long start = tri_off(k, n);
-    const long long end = start + (n - k - 1);
-    const long long base_c = k + 1 - start;  // column of flat index q is q + base_c
-    u64 best = kNoKey;
-    long long cnt = 0;
+    const int lane = threadIdx.x & 31;
+    const long long start = tri_off(r, n);
+    const long long end = start + (n - r - 1);
+    const long long base_c = r + 1 - start;  // column of flat index q is q + base_c
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
     long long a0 = p.aligned16 ? ((start + 3) & ~3LL) : end;
     if (a0 > end)
         a0 = end;
     const long long a1 = a0 + ((end - a0) & ~3LL);
-    // scalar head and tail
-    for (long long q = start + threadIdx.x; q < a0; q += kThreads) {
-        const unsigned c = (unsigned)(q + base_c);
-        if ((bitmap[c >> 5] >> (c & 31)) & 1u) {
-            const u64 key = make_key(__ldcg(p.D + q), c);
-            best = key < best ? key : best;
-            ++cnt;
-        }
-    }
-    for (long long q = a1 + threadIdx.x; q < end; q += kThreads) {
-        const unsigned c = (unsigned)(q + base_c);
-        if ((bitmap[c >> 5] >> (c & 31)) & 1u) {
-            const u64 key = make_key(__ldcg(p.D + q), c);
-            best = key < best ? key : best;
-            ++cnt;
-        }
-    }
-    for (long long q = a0 + 4 * (long long)threadIdx.x; q < a1; q += 4 * kThreads) {
-        const float4 x = __ldcg(reinterpret_cast<const float4 *>(p.D + q));
-        const float xv[4] = {x.x, x.y, x.z, x.w};
+    for (long long q = start + lane; q < a0; q += 32)
+        init_cell(__ldcg(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
+    for (long long q = a1 + lane; q < end; q += 32)
+        init_cell(__ldcg(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
+    // 128-bit body, four loads in flight per lane
+    long long q = a0 + 4 * lane;
+    for (; q + 3 * 128 < a1; q += 4 * 128) {
+        float4 x[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const unsigned c = (unsigned)(q + e + base_c);
-            if ((bitmap[c >> 5] >> (c & 31)) & 1u) {
-                const u64 key = make_key(xv[e], c);
-                best = key < best ? key : best;
-                ++cnt;
-            }
+        for (int u = 0; u < 4; ++u)
+            x[u] = __ldcg(reinterpret_cast<const float4 *>(p.D + q + 128 * u));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long qq = q + 128 * u;
+            const unsigned c = (unsigned)(qq + base_c);
+            init_cell(x[u].x, qq, c, p, L, bad);
+            init_cell(x[u].y, qq + 1, c + 1, p, L, bad);
+            init_cell(x[u].z, qq + 2, c + 2, p, L, bad);
+            init_cell(x[u].w, qq + 3, c + 3, p, L, bad);
         }
     }
-    live += cnt;
-    return block_u64_min(best, sh);
+    for (; q < a1; q += 128) {
+        const float4 x = __ldcg(reinterpret_cast<const float4 *>(p.D + q));
+        const unsigned c = (unsigned)(q + base_c);
+        init_cell(x.x, q, c, p, L, bad);
+        init_cell(x.y, q + 1, c + 1, p, L, bad);
+        init_cell(x.z, q + 2, c + 2, p, L, bad);
+        init_cell(x.w, q + 3, c + 3, p, L, bad);
+    }
+    warp_topk(L, out);
+}
+
+// K smallest keys of row r over live columns, computed by the whole CTA
+// (for a row whose cache empties before its refill arrives).  Adds the live
+// cells read to `live_cells`.  Result in sh.tko.
+__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared &sh,
+                               long long &live_cells)
+{
+    const long long n = p.n;
+    const long long start = tri_off(r, n);
+    const long long end = start + (n - r - 1);
+    const long long base_c = r + 1 - start;
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
+    long long cnt = 0;
+    for (long long q = start + threadIdx.x; q < end; q += kThreads) {
+        const long long c = q + base_c;
+        if (live(bitmap, c)) {
+            list_insert(L, make_key(__ldcg(p.D + q), (unsigned)c));
+            ++cnt;
+        }
+    }
+    live_cells += cnt;
+    block_topk(L, sh);
+}
+
+__device__ __forceinline__ void store_list(u64 *dst, const u64 *src)
+{
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        dst[q] = src[q];
 }
 
 __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
@@ -375,18 +400,26 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     const int G = p.G;
     const int b = blockIdx.x;
     const int tid = threadIdx.x;
-    const long long nb = (n + kRowBlock - 1) / kRowBlock;     // row blocks
+    const int lane = tid & 31, warp = tid >> 5;
+    const long long nb = (n + kRowBlock - 1) / kRowBlock;      // row blocks
     const long long my_blocks = b < nb ? (nb - b + G - 1) / G : 0;
-    const int R = (int)(my_blocks * kRowBlock);                // owned row slots
+    const int R = (int)(my_blocks * kRowBlock);                 // owned row slots
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
 
+    // dynamic shared memory: liveness bitmap, then per owned slot: cache keys,
+    // bound, last update key, size, key count, pending refill (merge, slot),
+    // and the list of rows to rescan at once
     unsigned *bitmap = reinterpret_cast<unsigned *>(smem_raw);
-    u64 *rkey = reinterpret_cast<u64 *>(smem_raw + ((nwords * 4 + 15) & ~15LL));
-    int *rsize = reinterpret_cast<int *>(rkey + Rmax);
-    int *rlist = rsize + Rmax;
+    u64 *ck = reinterpret_cast<u64 *>(smem_raw + ((nwords * 4 + 15) & ~15LL));
+    u64 *cB = ck + Rmax * K;
+    u64 *upd = cB + Rmax;
+    int *rsize = reinterpret_cast<int *>(upd + Rmax);
+    int *ccnt = rsize + Rmax;
+    int *pend_t = ccnt + Rmax;
+    int *pend_s = pend_t + Rmax;
+    int *rlist = pend_s + Rmax;
 
-    // global row of owned slot l, and (owner, slot) of a global row
     auto row_of = [&](int l) -> long long {
         return (long long)((long long)b + (long long)G * (l >> 5)) * kRowBlock + (l & 31);
     };
@@ -397,19 +430,68 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
 
     // ---- setup
     for (long long w = tid; w < nwords; w += kThreads) {
-        const long long lo = w * 32;
-        const long long live = n - lo;
-        bitmap[w] = live >= 32 ? 0xffffffffu : ((1u << live) - 1u);
+        const long long live_n = n - w * 32;
+        bitmap[w] = live_n >= 32 ? 0xffffffffu : ((1u << live_n) - 1u);
     }
-    for (int l = tid; l < R; l += kThreads)
+    for (int l = tid; l < R; l += kThreads) {
         rsize[l] = 1;
+        pend_t[l] = -1;
+        upd[l] = kNoKey;
+    }
     for (long long r = (long long)b * kThreads + tid; r < n; r += (long long)G * kThreads)
         p.size_g[r] = 1;
-    if (tid == 0)
+    if (tid == 0) {
         sh.nresc = 0;
+        sh.ninst = 0;
+        sh.nexec = 0;
+    }
 
+    // ---- phase 0: validate the matrix and fill the caches of owned rows
+    // (one warp per owned row; the rows of a CTA are spread over the whole
+    // triangle, so every CTA reads about the same number of cells)
+    {
+        int bad = 0;
+        for (int l = warp; l < R; l += kWarps) {
+            const long long r = row_of(l);
+            u64 top[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                top[q] = kNoKey;
+            if (r < n - 1)
+                warp_row_topk(p, r, top, bad);
+            if (lane == 0) {
+                store_list(ck + (size_t)l * K, top);
+                const int c = list_count(top);
+                ccnt[l] = c;
+                cB[l] = c == K ? top[K - 1] : kNoKey;
+            }
+        }
+        if (bad)
+            atomicCAS(p.status, 0, kErrInput);
+    }
+    __syncthreads();
+
+    long long st_updates = 0, st_resc_cells = 0, st_fill_cells = 0;
+    long long st_rescans = 0, st_fills = 0, st_installs = 0;
+
+    // first candidates: each CTA's smallest cached key
+    {
+        Cand c = {kNoKey, 0xffffffffu};
+        for (int l = tid; l < R; l += kThreads) {
+            if (ccnt[l] > 0) {
+                const u64 k = ck[(size_t)l * K];
+                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
+                cand_min(c, o);
+            }
+        }
+        c = block_cand_min(c, sh);
+        if (tid == 0) {
+            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + b);
+            __stcg(dst, make_ulonglong2(c.A, 0ull));
+            __stcg(dst + 1, make_ulonglong2((u64)c.c, 0ull));
+        }
+    }
     unsigned epoch = 0;
-    initial_scan(p);
     if (b == p.skip_arrive_cta)
         return;
     if (!grid_sync(p, epoch, sh))
@@ -420,49 +502,46 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     if (sh.flag != 0)
         return;
 
-    for (int l = tid; l < R; l += kThreads) {
-        const long long r = row_of(l);
-        rkey[l] = r < n ? __ldcg(p.rowkey_g + r) : kNoKey;
-    }
-    __syncthreads();
-
-    long long st_updates = 0, st_rescan_live = 0, st_rescans = 0;
-
-    // first records: each CTA's smallest row key
-    {
-        Cand c = {kNoKey, 0xffffffffu, kNoKey};
-        for (int l = tid; l < R; l += kThreads) {
-            const u64 k = rkey[l];
-            if (k != kNoKey) {
-                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k, kNoKey};
-                cand_min(c, o);
-            }
-        }
-        c = block_cand_min(c, sh);
-        if (tid == 0) {
-            ulonglong2 w0 = make_ulonglong2(c.A, c.K);
-            ulonglong2 w1 = make_ulonglong2((u64)c.c, 0ull);
-            __stcg(reinterpret_cast<ulonglong2 *>(p.recs + b), w0);
-            __stcg(reinterpret_cast<ulonglong2 *>(p.recs + b) + 1, w1);
-        }
-    }
-    if (!grid_sync(p, epoch, sh))
-        return;
-
-    int par = 0;
     long long prev_i = -1;
     int carried = 0;  // size of the cluster in slot prev_i after its merge
 
     for (long long t = 0; t < n - 1; ++t) {
-        // ---- Section 4 step 1: global minimum from the G records
-        Cand mine = {kNoKey, 0xffffffffu, kNoKey};
+        const int par = (int)(t & 1);
+
+        // ---- exchange: candidates, the survivor row's lists, refill requests
+        const bool own_prev = prev_i >= 0 && owner_of(prev_i) == b;
+        Cand mine = {kNoKey, 0xffffffffu};
+        u64 sl[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            sl[q] = kNoKey;
         if (tid < G) {
-            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.recs + par * G + tid);
+            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.cand + par * G + tid);
             const ulonglong2 w0 = __ldcg(src);
             const ulonglong2 w1 = __ldcg(src + 1);
             mine.A = w0.x;
-            mine.K = w0.y;
             mine.c = (unsigned)w1.x;
+            if (own_prev) {
+                const ulonglong2 *s2 =
+                    reinterpret_cast<const ulonglong2 *>(p.islice + ((size_t)par * G + tid) * K);
+#pragma unroll
+                for (int q = 0; q < K / 2; ++q) {
+                    const ulonglong2 v = __ldcg(s2 + q);
+                    sl[2 * q] = v.x;
+                    sl[2 * q + 1] = v.y;
+                }
+            }
+        }
+        // requests made in the previous merge are served in this one
+        const int rbuf = (int)((t + 2) % 3);
+        if (t >= 1 && tid >= kThreads - 1 - kMaxReq) {
+            if (tid == kThreads - 1) {
+                const int cnt = __ldcg(p.nreq + rbuf);
+                sh.nexec = cnt < kMaxReq ? cnt : kMaxReq;
+            } else {
+                const int s = tid - (kThreads - 1 - kMaxReq);
+                sh.exec_row[s] = __ldcg(p.req + rbuf * kMaxReq + s);
+            }
         }
         const Cand best = block_cand_min(mine, sh);
         const long long i = (long long)(best.A & 0xffffffffull);
@@ -475,18 +554,73 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             return;
         }
 
-        if (tid == 0) {
-            if (prev_i >= 0 && owner_of(prev_i) == b) {
-                rkey[slot_of(prev_i)] = best.K;        // survivor row reassembled
-                __stcg(p.size_g + prev_i, carried);    // deferred size write
+        // survivor of the previous merge: merge the G partial lists of its row
+        if (own_prev) {
+            block_topk(sl, sh);
+            if (tid == 0) {
+                const int l = slot_of(prev_i);
+                store_list(ck + (size_t)l * K, sh.tko);
+                const int c = list_count(sh.tko);
+                ccnt[l] = c;
+                cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
+                __stcg(p.size_g + prev_i, carried);  // deferred size write
             }
+        }
+
+        // refills served in the previous merge: merge the partial lists, then
+        // apply that merge's update to the row's one changed cell
+        const int ninst = sh.ninst;
+        for (int s = 0; s < ninst; ++s) {
+            const int l = sh.inst_slot[s];
+            u64 L[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                L[q] = kNoKey;
+            if (tid < G) {
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(
+                    p.parts + (((size_t)(par ^ 1) * G + tid) * kMaxReq + pend_s[l]) * K);
+#pragma unroll
+                for (int q = 0; q < K / 2; ++q) {
+                    const ulonglong2 v = __ldcg(src + q);
+                    L[2 * q] = v.x;
+                    L[2 * q + 1] = v.y;
+                }
+            }
+            block_topk(L, sh);
+            if (tid == 0) {
+                u64 M[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q)
+                    M[q] = sh.tko[q];
+                int c = list_count(M);
+                u64 B = c == K ? M[K - 1] : kNoKey;
+                const u64 x = upd[l];
+                if (x != kNoKey && x <= B) {
+                    list_insert(M, x);
+                    if (c == K)
+                        B = M[K - 1];
+                    else
+                        ++c;
+                }
+                store_list(ck + (size_t)l * K, M);
+                ccnt[l] = c;
+                cB[l] = B;
+                pend_t[l] = -1;
+            }
+        }
+        st_installs += ninst;
+
+        if (tid == 0) {
             if (b == 0) {
                 p.merges[2 * t] = (int32_t)i;
                 p.merges[2 * t + 1] = (int32_t)j;
                 p.heights[t] = h;
+                // the count buffer served two merges ago is free again
+                __stcg(p.nreq + (int)((t + 1) % 3), 0);
             }
-            bitmap[j >> 5] &= ~(1u << (j & 31));       // step 2: slot j retires
+            bitmap[j >> 5] &= ~(1u << (j & 31));  // Section 4 step 2: slot j retires
             sh.nresc = 0;
+            sh.ninst = 0;
         }
         int ni = 1, nj = 1;
         if (p.linkage >= 2) {
@@ -506,12 +640,14 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             ai = __fdiv_rn((float)ni, sum);
             aj = __fdiv_rn((float)nj, sum);
         }
-        u64 islice = kNoKey;
+        u64 il[K];  // this thread's smallest new cells of the survivor row
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            il[q] = kNoKey;
+        const int rb_now = (int)(t % 3);
         for (int l = tid; l < R; l += kThreads) {
             const long long k = row_of(l);
-            if (k >= n || k == i || k == j)
-                continue;
-            if (!((bitmap[k >> 5] >> (k & 31)) & 1u))
+            if (k >= n || k == i || k == j || !live(bitmap, k))
                 continue;
             const long long pki = pair_idx(k, i, n);
             const long long pkj = pair_idx(k, j, n);
@@ -530,73 +666,139 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             s = __fadd_rn(s, __fmul_rn(ga, fabsf(__fsub_rn(a, bb))));
             __stcg(p.D + pki, s);
             ++st_updates;
-            if (k < i) {
-                // row k: cell (k,i) changed, cell (k,j) left
-                const u64 old = rkey[l];
-                const unsigned arg = (unsigned)old;
-                const u64 nkey = make_key(s, (unsigned)i);
-                if (arg == (unsigned)i || arg == (unsigned)j) {
-                    if (nkey <= old) {
-                        rkey[l] = nkey;
-                    } else {
-                        rkey[l] = kNoKey;
-                        rlist[atomicAdd(&sh.nresc, 1)] = l;
-                    }
-                } else if (nkey < old) {
-                    rkey[l] = nkey;
-                }
-            } else {
+            if (k > i) {
                 // cell (i,k) belongs to the survivor row i
-                const u64 key = make_key(s, (unsigned)k);
-                islice = key < islice ? key : islice;
-                if (k < j && (unsigned)rkey[l] == (unsigned)j) {
-                    rkey[l] = kNoKey;
-                    rlist[atomicAdd(&sh.nresc, 1)] = l;
+                list_insert(il, make_key(s, (unsigned)k));
+                upd[l] = kNoKey;
+                if (k > j)
+                    continue;  // row k holds neither column i nor column j
+            }
+            // row k loses column j; if k < i its cell (k,i) changed as well
+            u64 C[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                C[q] = ck[(size_t)l * K + q];
+                const unsigned col = (unsigned)C[q];
+                if (col == (unsigned)j || (k < i && col == (unsigned)i))
+                    C[q] = kNoKey;
+            }
+            sort4(C);
+            int c = list_count(C);
+            u64 B = cB[l];
+            if (k < i) {
+                const u64 x = make_key(s, (unsigned)i);
+                upd[l] = x;
+                if (x <= B) {
+                    list_insert(C, x);
+                    if (c == K)
+                        B = C[K - 1];
+                    else
+                        ++c;
+                }
+            }
+            store_list(ck + (size_t)l * K, C);
+            ccnt[l] = c;
+            cB[l] = B;
+            if (c == 0) {
+                rlist[atomicAdd(&sh.nresc, 1)] = l;
+                pend_t[l] = -1;
+            } else if (c <= kRefillAt && pend_t[l] < 0) {
+                const int s2 = atomicAdd(p.nreq + rb_now, 1);
+                if (s2 < kMaxReq) {
+                    p.req[rb_now * kMaxReq + s2] = (int)k;
+                    pend_t[l] = (int)t;
+                    pend_s[l] = s2;
                 }
             }
         }
         if (tid == 0) {
-            if (owner_of(j) == b)
-                rkey[slot_of(j)] = kNoKey;
+            if (owner_of(j) == b) {
+                const int l = slot_of(j);
+                ccnt[l] = 0;
+                pend_t[l] = -1;
+            }
             if (owner_of(i) == b) {
-                rkey[slot_of(i)] = kNoKey;  // reassembled from the records next merge
-                rsize[slot_of(i)] = ni + nj;
+                const int l = slot_of(i);
+                ccnt[l] = 0;  // rebuilt from the partial lists after the barrier
+                pend_t[l] = -1;
+                rsize[l] = ni + nj;
             }
         }
         __syncthreads();
 
-        // ---- cache repair: rows that lost their minimum
+        // ---- rows whose cache emptied before a refill arrived
         const int nresc = sh.nresc;
         for (int q = 0; q < nresc; ++q) {
             const int l = rlist[q];
-            const u64 m = rescan_row(p, row_of(l), bitmap, sh, st_rescan_live);
-            if (tid == 0)
-                rkey[l] = m;
+            block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
+            if (tid == 0) {
+                store_list(ck + (size_t)l * K, sh.tko);
+                const int c = list_count(sh.tko);
+                ccnt[l] = c;
+                cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
+            }
         }
-        if (tid == 0)
-            st_rescans += nresc;
-        __syncthreads();
+        st_rescans += nresc;
 
-        // ---- publish this CTA's candidate and its part of the survivor row
-        Cand c = {kNoKey, 0xffffffffu, islice};
-        if (islice != kNoKey) {
-            c.A = (islice & 0xffffffff00000000ull) | (u64)i;
-            c.c = (unsigned)islice;
+        // ---- serve the refills asked for in the previous merge: the K
+        // smallest keys of the row over this CTA's live columns, leaving out
+        // columns i and j (their cells change in this merge)
+        const int nexec = sh.nexec;
+        for (int s = 0; s < nexec; ++s) {
+            const long long r = sh.exec_row[s];
+            if (r == i || r == j || r < 0 || r >= n)
+                continue;  // the owner drops this refill
+            u64 L[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                L[q] = kNoKey;
+            const long long base = tri_off(r, n) - r - 1;  // cell (r, c) at base + c
+            for (int l = tid; l < R; l += kThreads) {
+                const long long c = row_of(l);
+                if (c > r && c < n && c != i && c != j && live(bitmap, c)) {
+                    list_insert(L, make_key(__ldcg(p.D + base + c), (unsigned)c));
+                    ++st_fill_cells;
+                }
+            }
+            block_topk(L, sh);
+            if (tid < K / 2) {
+                ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
+                    p.parts + (((size_t)par * G + b) * kMaxReq + s) * K);
+                __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
+            }
+        }
+        st_fills += nexec;
+
+        // ---- publish: this CTA's part of the survivor row and its candidate
+        block_topk(il, sh);
+        Cand c = {kNoKey, 0xffffffffu};
+        if (tid == 0 && sh.tko[0] != kNoKey) {
+            c.A = (sh.tko[0] & 0xffffffff00000000ull) | (u64)i;
+            c.c = (unsigned)sh.tko[0];
+        }
+        if (tid < K / 2) {
+            ulonglong2 *dst =
+                reinterpret_cast<ulonglong2 *>(p.islice + ((size_t)(par ^ 1) * G + b) * K);
+            __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
         }
         for (int l = tid; l < R; l += kThreads) {
-            const u64 k = rkey[l];
-            if (k != kNoKey) {
-                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k, kNoKey};
+            if (ccnt[l] > 0) {
+                const u64 k = ck[(size_t)l * K];
+                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
                 cand_min(c, o);
+            }
+            // refills served in this merge are installed at the next one
+            // (pend_t is -1 when no refill is pending, so merge 0 has none)
+            if (t >= 1 && pend_t[l] == (int)t - 1) {
+                const int s = atomicAdd(&sh.ninst, 1);
+                sh.inst_slot[s] = l;
             }
         }
         c = block_cand_min(c, sh);
-        par ^= 1;
         if (tid == 0) {
-            ulonglong2 w0 = make_ulonglong2(c.A, c.K);
-            ulonglong2 w1 = make_ulonglong2((u64)c.c, 0ull);
-            __stcg(reinterpret_cast<ulonglong2 *>(p.recs + par * G + b), w0);
-            __stcg(reinterpret_cast<ulonglong2 *>(p.recs + par * G + b) + 1, w1);
+            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + (par ^ 1) * G + b);
+            __stcg(dst, make_ulonglong2(c.A, 0ull));
+            __stcg(dst + 1, make_ulonglong2((u64)c.c, 0ull));
         }
         prev_i = i;
         carried = ni + nj;
@@ -605,12 +807,18 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     }
 
     if (p.stats) {
-        atomicAdd(reinterpret_cast<u64 *>(p.stats + 1), (u64)st_rescan_live);
-        atomicAdd(reinterpret_cast<u64 *>(p.stats + 2), (u64)st_updates);
-        if (tid == 0)
-            atomicAdd(reinterpret_cast<u64 *>(p.stats + 0), (u64)st_rescans);
-        if (b == 0 && tid == 0)
-            p.stats[3] = G;
+        u64 *S = reinterpret_cast<u64 *>(p.stats);
+        atomicAdd(S + 1, (u64)st_resc_cells);
+        atomicAdd(S + 2, (u64)st_updates);
+        atomicAdd(S + 5, (u64)st_fill_cells);
+        if (tid == 0) {
+            atomicAdd(S + 0, (u64)st_rescans);
+            atomicAdd(S + 6, (u64)st_installs);
+            if (b == 0) {
+                S[3] = (u64)G;
+                S[4] = (u64)st_fills;
+            }
+        }
     }
 }
 
@@ -621,12 +829,14 @@ size_t merge_smem_bytes(long long n, int G)
     const long long nb = (n + kRowBlock - 1) / kRowBlock;
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * 8 + Rmax * 4 + Rmax * 4);
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * (8 * K + 8 + 8 + 4 * 5));
 }
 
 bool merge_config_ok(long long n, int G, int num_sms)
 {
-    if (G < 1 || G > num_sms)
+    // threads [kThreads-1-kMaxReq, kThreads) read the refill requests, the
+    // first G threads the candidates: the two sets must not overlap
+    if (G < 1 || G > num_sms || G > kThreads - 1 - kMaxReq)
         return false;
     int dev = 0, limit = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||

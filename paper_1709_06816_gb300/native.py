@@ -60,7 +60,7 @@ def load(path: str = LIB_PATH):
             f.restype = ctypes.c_int
         lib.lw_wait.argtypes = [vp]
         lib.lw_wait.restype = ctypes.c_int
-        lib.lw_get_stats.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.lw_get_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
         lib.lw_get_stats.restype = ctypes.c_int
         lib.lw_set_option.argtypes = [vp, ctypes.c_int, i64]
         lib.lw_set_option.restype = ctypes.c_int
@@ -126,11 +126,12 @@ def lw_wait(ctx: int) -> None:
 
 def lw_get_stats(ctx: int) -> dict:
     lib = load()
-    a = (ctypes.c_int64 * 4)()
-    s = lib.lw_get_stats(ctx, a)
+    a = (ctypes.c_int64 * 8)()
+    s = lib.lw_get_stats(ctx, a, 8)
     if s != 0:
         raise LwError(s, "lw_get_stats")
-    return {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3]}
+    return {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3],
+            "refills": a[4], "refill_cells": a[5], "installs": a[6]}
 
 
 def lw_set_option(ctx: int, option: int, value: int) -> None:
