@@ -126,7 +126,11 @@ lw_status lw_wait(lw_ctx *ctx);
  *   [3] CTAs of the persistent grid,
  *   [4] row refills served by all CTAs together,
  *   [5] live cells read by those refills,
- *   [6] refills installed by the rows' owners.
+ *   [6] refills installed by the rows' owners,
+ *   [8..13] with LW_OPT_PHASE_TIMES on: wall-clock nanoseconds summed over
+ *       the CTAs of the grid, per phase of a merge: [8] barrier wait,
+ *       [9] exchange + global minimum, [10] survivor row and refill
+ *       installs, [11] update, [12] rescans + publish, [13] refill service.
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 
@@ -140,10 +144,11 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *                     multi-CTA grid returns before the first grid barrier,
  *                     so the other CTAs' bounded waits run out and the call
  *                     reports LW_ERR_TIMEOUT with the context still usable;
- *                     -1 switches it off (the default).
+ *                     -1 switches it off (the default);
+ *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..13]).
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
-enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2, LW_OPT_TEST_SKIP_ARRIVE = 3 };
+enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2, LW_OPT_TEST_SKIP_ARRIVE = 3, LW_OPT_PHASE_TIMES = 4 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
 /*
@@ -156,7 +161,7 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
  * application's plug-in, or in a loop that must never enter the allocator.
  * It needs no lw_ctx and allocates nothing, host or device: the kernel's
  * scratch (cluster sizes, exchange records, barrier words) is a fixed
- * file-scope device array of 512 KB in liblw.so, created when the library is
+ * file-scope device array of 1 MB in liblw.so, created when the library is
  * loaded on a device and held by every device that loads it until the
  * process exits.
  *   dist, merges_out, heights_out  DEVICE pointers as for lw_cluster (dist is

@@ -22,6 +22,7 @@ struct lw_ctx {
     int grid_opt = 0;
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
+    int phase_timing = 0;
 
     // device workspace
     void *ws = nullptr;
@@ -157,19 +158,18 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     p.cand = reinterpret_cast<lw::Rec *>(ws + L.cand);
     p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
     p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
-    p.req = reinterpret_cast<int *>(ws + L.req);
-    p.nreq = reinterpret_cast<int *>(ws + L.nreq);
     p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
     p.status = reinterpret_cast<int *>(ws + L.status);
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
     p.skip_arrive_cta = (ctx->test_skip_arrive >= 0 && ctx->test_skip_arrive < G && G > 1)
                             ? ctx->test_skip_arrive : -1;
+    p.timing = ctx->phase_timing;
     ctx->d_status = p.status;
     ctx->d_stats = p.stats;
 
     cudaError_t e;
-    // request counts, barrier, status and stats words are contiguous
+    // barrier, status and stats words are contiguous
     if ((e = cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
     if ((e = lw::launch_merge(p, ctx->stream)) != cudaSuccess)
@@ -408,6 +408,9 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
         return LW_OK;
     case LW_OPT_TEST_SKIP_ARRIVE:
         ctx->test_skip_arrive = value < 0 ? -1 : (int)value;
+        return LW_OK;
+    case LW_OPT_PHASE_TIMES:
+        ctx->phase_timing = value != 0;
         return LW_OK;
     default:
         return LW_ERR_INVALID_ARG;

@@ -13,20 +13,21 @@ constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
 constexpr int kCacheKeys = 4;            // smallest keys cached per row
 constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
 constexpr int kMaxReq = 32;              // refill requests served per merge
-constexpr int kStats = 8;
+constexpr int kReqPerCta = 4;            // refill requests one CTA may make per merge
+constexpr int kStats = 16;
 constexpr uint64_t kNoKey = ~0ull;
 
 // Status words written by the kernel (values match lw_status).
 enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
 
-// One CTA's candidate for the global minimum of a merge, 32 bytes:
-//   A = (bits(value) << 32) | row,  c = column  of the CTA's smallest cell.
+// One CTA's record for the next merge, 32 bytes: its candidate for the
+// global minimum, A = (bits(value) << 32) | row and c = column of its
+// smallest cell, and the rows (at most kReqPerCta) that ask for a refill.
 struct __align__(16) Rec {
     unsigned long long A;
-    unsigned long long pad0;
     unsigned int c;
-    unsigned int pad1;
-    unsigned long long pad2;
+    unsigned int nreq;
+    int req[kReqPerCta];
 };
 
 struct MergeParams {
@@ -40,9 +41,7 @@ struct MergeParams {
     int *size_g;                   // [n] cluster sizes
     Rec *cand;                     // [2][G] candidates (double-buffered by merge parity)
     unsigned long long *islice;    // [2][G][kCacheKeys] survivor-row partial top-K
-    unsigned long long *parts;     // [2][G][kMaxReq][kCacheKeys] refill partial top-K
-    int *req;                      // [3][kMaxReq] rows asking for a refill
-    int *nreq;                     // [3] request counts (zero at launch)
+    unsigned long long *parts;     // [3][G][kMaxReq][kCacheKeys] refill partial top-K
     unsigned int *bar;             // grid barrier counter (zero at launch)
     int *status;                   // [4] status word [0]; barrier that gave up [1]
     long long *stats;              // [kStats] counters, see lw_get_stats
@@ -50,13 +49,14 @@ struct MergeParams {
     int skip_arrive_cta;           // failure-detection test: this CTA never reaches the
                                    // first barrier (-1 = off), so the others' bounded
                                    // wait runs out and reports LW_ERR_TIMEOUT
+    int timing;                    // accumulate per-phase wall-clock time in stats[8..13]
 };
 
 // Byte offsets of the merge kernel's global scratch inside one workspace
 // block (every part 256-byte aligned).  The words from `zero` to `total`
-// (request counts, barrier, status, stats) must be zero at launch.
+// (barrier, status, stats) must be zero at launch.
 struct WorkspaceLayout {
-    size_t size, cand, islice, parts, req, zero, nreq, bar, status, stats, total;
+    size_t size, cand, islice, parts, zero, bar, status, stats, total;
 };
 
 inline WorkspaceLayout workspace_layout(long long n, int G)
@@ -67,10 +67,8 @@ inline WorkspaceLayout workspace_layout(long long n, int G)
     L.size = off;   off = up(off + sizeof(int) * (size_t)n);
     L.cand = off;   off = up(off + sizeof(Rec) * 2 * (size_t)G);
     L.islice = off; off = up(off + 8 * kCacheKeys * 2 * (size_t)G);
-    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 2 * (size_t)G);
-    L.req = off;    off = up(off + sizeof(int) * 3 * kMaxReq);
+    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 3 * (size_t)G);
     L.zero = off;
-    L.nreq = off;   off = up(off + sizeof(int) * 3);
     L.bar = off;    off = up(off + 256);
     L.status = off; off = up(off + 4 * sizeof(int));
     L.stats = off;  off = up(off + kStats * sizeof(long long));

@@ -14,17 +14,19 @@
 // same map, those columns.  The owner of row k
 //   - keeps, in shared memory, the kCacheKeys smallest keys of row k
 //     (key = (value bits << 32) | column, over live columns c > k) and a bound
-//     B: every live cell of the row outside the cache has a key above B;
+//     B: every live cell of the row outside the cache has a key above B
+//     (B = "none" when the cache holds every live cell of the row);
 //   - applies the update of Section 4 step 3 for k at every merge: reads D(k,i),
 //     D(k,j), writes D(k,i+j) into D(k,i), and maintains row k's cache
 //     (drops columns i and j, inserts the new cell (k,i) when it is <= B).
 // The row minimum is exact while the cache is not empty.  A row whose cache
-// runs low asks for a refill; in the NEXT merge every CTA scans its own
-// columns of that row and publishes a partial top-K list, and one merge later
-// the owner merges the lists (applying the one update that happened in
-// between).  So no CTA scans a long row alone on the critical path; only a
-// row whose cache empties before its refill lands is rescanned at once by
-// its owner.
+// runs low asks for a refill; in the barrier window of the NEXT merge (after
+// a CTA has arrived at the grid barrier and before it waits) one warp of
+// every CTA scans that CTA's columns of the row and publishes a partial
+// top-K list, and two merges after the request the owner merges the lists
+// and replays the two updates that happened meanwhile.  So row scans stay
+// off the critical path; only a row whose cache empties before its refill
+// lands is rescanned at once by its owner.
 //
 // The survivor row i is rewritten by every CTA (one cell per owned k > i);
 // each CTA folds its part of row i into its candidate and publishes its
@@ -32,8 +34,9 @@
 // barrier.
 //
 // One grid barrier per merge:
-//   [barrier] read G candidates -> global minimum (value, i, j) -> emit step
-//   -> update + cache upkeep + refill scans -> publish records -> [barrier]
+//   [wait] read G candidates (+ survivor lists, refill lists, requests)
+//   -> global minimum (value, i, j) -> emit step -> update + cache upkeep
+//   -> publish candidate and survivor list -> [arrive] serve refills [wait]
 //
 // Exact arithmetic: every product and sum of the update uses __fmul_rn /
 // __fadd_rn / __fsub_rn (never contracted into FMA), the coefficient
@@ -44,10 +47,11 @@
 //
 // Memory model.  L1 is not coherent across SMs, so every load of data that
 // another CTA may have written (matrix cells, records, sizes) is an L2 load
-// (ld.global.cg) and every store bypasses L1 (st.global.cg).  The barrier is
-// the cooperative-groups pattern: __syncthreads, one thread fences, arrives
-// with a release add and spins with acquire loads.  Each spin is bounded by a
-// wall-clock limit after which the kernel records LW_ERR_TIMEOUT and returns.
+// (ld.global.cg) and every store bypasses L1 (st.global.cg).  The barrier:
+// __syncthreads, then one thread arrives with a release add (cumulative over
+// the CTA's writes ordered before it by the __syncthreads) and later spins
+// with acquire loads.  Each spin is bounded by a wall-clock limit after which
+// the kernel records LW_ERR_TIMEOUT and returns.
 
 #include "lw_internal.h"
 
@@ -58,7 +62,6 @@ namespace {
 
 typedef unsigned long long u64;
 constexpr int K = kCacheKeys;
-static_assert(K == 4, "the cache upkeep below sorts four keys with a fixed network");
 
 __device__ __forceinline__ long long tri_off(long long r, long long n)
 {
@@ -120,17 +123,19 @@ __device__ __forceinline__ void list_insert(u64 (&L)[K], u64 x)
         cswap(L[q], x);
 }
 
-// Sort four keys (removed entries are kNoKey and sink to the end).
-__device__ __forceinline__ void sort4(u64 (&L)[K])
+// Re-sort a sorted list in which at most two entries were replaced by kNoKey:
+// two bubble passes carry both holes to the end.
+__device__ __forceinline__ void close_holes(u64 (&L)[K])
 {
-    cswap(L[0], L[1]);
-    cswap(L[2], L[3]);
-    cswap(L[0], L[2]);
-    cswap(L[1], L[3]);
-    cswap(L[1], L[2]);
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+        for (int q = 0; q + 1 < K; ++q)
+            cswap(L[q], L[q + 1]);
+    }
 }
 
-__device__ __forceinline__ int list_count(const u64 (&L)[K])
+__device__ __forceinline__ int list_count(const u64 *L)
 {
     int c = 0;
 #pragma unroll
@@ -139,14 +144,14 @@ __device__ __forceinline__ int list_count(const u64 (&L)[K])
     return c;
 }
 
+// Warp-wide minimum of 64-bit keys with two hardware warp reductions: the
+// smallest high word, then the smallest low word among the lanes holding it.
 __device__ __forceinline__ u64 warp_u64_min(u64 v)
 {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const u64 o = __shfl_xor_sync(0xffffffffu, v, off);
-        v = o < v ? o : v;
-    }
-    return v;
+    const unsigned hi = (unsigned)(v >> 32);
+    const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? (unsigned)v : 0xffffffffu);
+    return ((u64)mhi << 32) | mlo;
 }
 
 // K smallest keys over the lists of a warp (keys are distinct or kNoKey).
@@ -177,29 +182,86 @@ __device__ __forceinline__ void cand_min(Cand &x, const Cand &y)
         x = y;
 }
 
+// Warp-wide lexicographic minimum of (value bits, row, column) with three
+// hardware warp reductions, each over the lanes that tie on the words before.
 __device__ __forceinline__ Cand warp_cand_min(Cand v)
 {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        Cand o;
-        o.A = __shfl_xor_sync(0xffffffffu, v.A, off);
-        o.c = __shfl_xor_sync(0xffffffffu, v.c, off);
-        cand_min(v, o);
-    }
-    return v;
+    const unsigned h = (unsigned)(v.A >> 32), r = (unsigned)v.A;
+    const unsigned mh = __reduce_min_sync(0xffffffffu, h);
+    const unsigned mr = __reduce_min_sync(0xffffffffu, h == mh ? r : 0xffffffffu);
+    const unsigned mc =
+        __reduce_min_sync(0xffffffffu, (h == mh && r == mr) ? v.c : 0xffffffffu);
+    Cand out;
+    out.A = ((u64)mh << 32) | mr;
+    out.c = mc;
+    return out;
 }
 
 struct Shared {
     Cand red[kWarps + 1];
     u64 tk[kWarps][K];
     u64 tko[K];
+    int wcnt[kWarps];        // per-warp request counts (prefix sums)
     int flag;
     int nresc;               // rows to rescan at once this merge
     int nexec;               // refill rows served this merge
     int exec_row[kMaxReq];
+    int my_off;              // where this CTA's requests landed in the list
+    int nmyreq[2];           // this CTA's requests, by merge parity
+    int myreq_l[2][kReqPerCta];
     int ninst;               // refills to install at the start of the next merge
     int inst_slot[kMaxReq];  // owned slots of those rows
 };
+
+// After the barrier: the global minimum over the G candidates, and the list
+// of rows to refill in this merge -- every CTA's requests in CTA order
+// (deterministic, the same in every CTA), cut at kMaxReq.  Thread t holds
+// CTA t's record (cnt requests in rq).  Sets sh.exec_row, sh.nexec and
+// sh.my_off (the position of this CTA's first request).
+__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], Shared &sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off)
+            inc += o;
+    }
+    v = warp_cand_min(v);
+    if (lane == 31)
+        sh.wcnt[warp] = inc;
+    if (lane == 0)
+        sh.red[warp] = v;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w)
+        base += sh.wcnt[w];
+    const int off0 = base + inc - cnt;
+#pragma unroll
+    for (int q = 0; q < kReqPerCta; ++q) {
+        if (q < cnt && off0 + q < kMaxReq)
+            sh.exec_row[off0 + q] = rq[q];
+    }
+    if ((int)threadIdx.x == (int)blockIdx.x)
+        sh.my_off = off0;
+    if (warp == 0) {
+        Cand w = {kNoKey, 0xffffffffu};
+        if (lane < kWarps)
+            w = sh.red[lane];
+        w = warp_cand_min(w);
+        int tot = lane < kWarps ? sh.wcnt[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            tot += __shfl_xor_sync(0xffffffffu, tot, off);
+        if (lane == 0) {
+            sh.red[kWarps] = w;
+            sh.nexec = tot < kMaxReq ? tot : kMaxReq;
+        }
+    }
+    __syncthreads();
+    return sh.red[kWarps];
+}
 
 __device__ Cand block_cand_min(Cand v, Shared &sh)
 {
@@ -247,18 +309,63 @@ __device__ void block_topk(u64 (&L)[K], Shared &sh)
     __syncthreads();
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false when the run must
-// stop (this CTA gave up waiting, or another CTA flagged an error).
-__device__ bool grid_sync(const MergeParams &p, unsigned &epoch, Shared &sh)
+// Both reductions a CTA publishes, in one pass: the candidate minimum (in
+// sh.red[kWarps]) and the K smallest survivor-row keys (in sh.tko).
+__device__ void block_publish(Cand c, u64 (&L)[K], Shared &sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 w[K];
+    warp_topk(L, w);
+    c = warp_cand_min(c);
+    if (lane == 0) {
+        sh.red[warp] = c;
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            sh.tk[warp][q] = w[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Cand x = {kNoKey, 0xffffffffu};
+        u64 M[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            M[q] = lane < kWarps ? sh.tk[lane][q] : kNoKey;
+        if (lane < kWarps)
+            x = sh.red[lane];
+        warp_topk(M, w);
+        x = warp_cand_min(x);
+        if (lane == 0) {
+            sh.red[kWarps] = x;
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                sh.tko[q] = w[q];
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide barrier, split in two so that a CTA can do work that nobody
+// waits for between arriving and waiting.  arrive: __syncthreads, then one
+// thread adds to the counter with release semantics (the CTA's writes so far
+// are published).  wait: that thread spins with acquire loads until every
+// CTA has arrived, bounded by a wall-clock limit; returns false when the run
+// must stop (this CTA gave up, or another CTA flagged an error).
+__device__ __forceinline__ void grid_arrive(const MergeParams &p, unsigned &epoch)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1;
+        if (p.G > 1)
+            red_release_add(p.bar, 1u);
+    }
+}
+
+__device__ bool grid_wait(const MergeParams &p, unsigned epoch, Shared &sh)
+{
+    if (threadIdx.x == 0) {
         int st = 0;
         if (p.G > 1) {
             const unsigned target = epoch * (unsigned)p.G;
-            __threadfence();
-            red_release_add(p.bar, 1u);
             const u64 t0 = global_ns();
             unsigned spins = 0;
             while (ld_acquire_u32(p.bar) < target) {
@@ -274,7 +381,6 @@ __device__ bool grid_sync(const MergeParams &p, unsigned &epoch, Shared &sh)
                     }
                 }
             }
-            __threadfence();
         }
         sh.flag = st;
     }
@@ -384,11 +490,21 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
     block_topk(L, sh);
 }
 
-__device__ __forceinline__ void store_list(u64 *dst, const u64 *src)
+__device__ __forceinline__ void load_list(u64 (&L)[K], const u64 *src)
 {
+    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
 #pragma unroll
-    for (int q = 0; q < K; ++q)
-        dst[q] = src[q];
+    for (int q = 0; q < K / 2; ++q) {
+        const ulonglong2 v = __ldcg(s2 + q);
+        L[2 * q] = v.x;
+        L[2 * q + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void publish_list(u64 *dst, const u64 *src, int tid)
+{
+    if (tid < K / 2)
+        __stcg(reinterpret_cast<ulonglong2 *>(dst) + tid, make_ulonglong2(src[2 * tid], src[2 * tid + 1]));
 }
 
 __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
@@ -407,14 +523,16 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
 
-    // dynamic shared memory: liveness bitmap, then per owned slot: cache keys,
-    // bound, last update key, size, key count, pending refill (merge, slot),
-    // and the list of rows to rescan at once
+    // dynamic shared memory: liveness bitmap, then per owned slot l: cache
+    // keys (key q of slot l at ck[q * Rmax + l]: consecutive threads read
+    // consecutive words), bound, the new key of cell (k, i) of the last two
+    // merges (by merge parity), size, key count, pending refill (merge, list
+    // position), and the list of rows to rescan at once
     unsigned *bitmap = reinterpret_cast<unsigned *>(smem_raw);
     u64 *ck = reinterpret_cast<u64 *>(smem_raw + ((nwords * 4 + 15) & ~15LL));
     u64 *cB = ck + Rmax * K;
-    u64 *upd = cB + Rmax;
-    int *rsize = reinterpret_cast<int *>(upd + Rmax);
+    u64 *upd = cB + Rmax;  // [2][Rmax]
+    int *rsize = reinterpret_cast<int *>(upd + 2 * Rmax);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
     int *pend_s = pend_t + Rmax;
@@ -427,6 +545,27 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     auto slot_of = [&](long long r) -> int {
         return (int)(((r / kRowBlock) / G) * kRowBlock + (r & 31));
     };
+    auto cache_load = [&](u64 (&L)[K], int l) {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            L[q] = ck[(size_t)q * Rmax + l];
+    };
+    auto cache_store = [&](int l, const u64 *L) {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            ck[(size_t)q * Rmax + l] = L[q];
+    };
+
+    // per-phase wall-clock totals of this CTA (thread 0), when timing is on
+    u64 ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
+    u64 tmark = 0;
+    auto lap = [&](u64 &acc) {
+        if (p.timing && threadIdx.x == 0) {
+            const u64 now = global_ns();
+            acc += now - tmark;
+            tmark = now;
+        }
+    };
 
     // ---- setup
     for (long long w = tid; w < nwords; w += kThreads) {
@@ -437,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
         rsize[l] = 1;
         pend_t[l] = -1;
         upd[l] = kNoKey;
+        upd[Rmax + l] = kNoKey;
     }
     for (long long r = (long long)b * kThreads + tid; r < n; r += (long long)G * kThreads)
         p.size_g[r] = 1;
@@ -444,6 +584,8 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
         sh.nresc = 0;
         sh.ninst = 0;
         sh.nexec = 0;
+        sh.nmyreq[0] = 0;
+        sh.nmyreq[1] = 0;
     }
 
     // ---- phase 0: validate the matrix and fill the caches of owned rows
@@ -460,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             if (r < n - 1)
                 warp_row_topk(p, r, top, bad);
             if (lane == 0) {
-                store_list(ck + (size_t)l * K, top);
+                cache_store(l, top);
                 const int c = list_count(top);
                 ccnt[l] = c;
                 cB[l] = c == K ? top[K - 1] : kNoKey;
@@ -474,12 +616,12 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     long long st_updates = 0, st_resc_cells = 0, st_fill_cells = 0;
     long long st_rescans = 0, st_fills = 0, st_installs = 0;
 
-    // first candidates: each CTA's smallest cached key
+    // first records: each CTA's smallest cached key, no refill requests
     {
         Cand c = {kNoKey, 0xffffffffu};
         for (int l = tid; l < R; l += kThreads) {
             if (ccnt[l] > 0) {
-                const u64 k = ck[(size_t)l * K];
+                const u64 k = ck[l];
                 Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
                 cand_min(c, o);
             }
@@ -487,63 +629,67 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
         c = block_cand_min(c, sh);
         if (tid == 0) {
             ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + b);
-            __stcg(dst, make_ulonglong2(c.A, 0ull));
-            __stcg(dst + 1, make_ulonglong2((u64)c.c, 0ull));
+            __stcg(dst, make_ulonglong2(c.A, (u64)c.c));
+            __stcg(dst + 1, make_ulonglong2(0ull, 0ull));
         }
     }
     unsigned epoch = 0;
     if (b == p.skip_arrive_cta)
         return;
-    if (!grid_sync(p, epoch, sh))
+    grid_arrive(p, epoch);
+    if (!grid_wait(p, epoch, sh))
         return;
     if (tid == 0)
         sh.flag = ld_relaxed_s32(p.status);
     __syncthreads();
     if (sh.flag != 0)
         return;
+    if (p.timing && tid == 0)
+        tmark = global_ns();
 
-    long long prev_i = -1;
-    int carried = 0;  // size of the cluster in slot prev_i after its merge
+    // the pair merged in merge t-1
+    long long i1 = -1, j1 = -1;
+    int carried = 0;  // size of the cluster in slot i1 after merge t-1
 
     for (long long t = 0; t < n - 1; ++t) {
         const int par = (int)(t & 1);
 
-        // ---- exchange: candidates, the survivor row's lists, refill requests
-        const bool own_prev = prev_i >= 0 && owner_of(prev_i) == b;
+        // ---- exchange: every CTA's record (candidate + refill requests),
+        // the survivor row's partial lists, the first refill to install --
+        // one round of loads, then one reduction
+        const bool own_prev = i1 >= 0 && owner_of(i1) == b;
+        const int ninst = sh.ninst;
+        const int pbuf = (int)((t + 1) % 3);  // refills served two merges ago
         Cand mine = {kNoKey, 0xffffffffu};
-        u64 sl[K];
+        int rcnt = 0;
+        int rq[kReqPerCta];
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+        for (int q = 0; q < kReqPerCta; ++q)
+            rq[q] = -1;
+        u64 sl[K], il0[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
             sl[q] = kNoKey;
+            il0[q] = kNoKey;
+        }
         if (tid < G) {
             const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.cand + par * G + tid);
             const ulonglong2 w0 = __ldcg(src);
             const ulonglong2 w1 = __ldcg(src + 1);
             mine.A = w0.x;
-            mine.c = (unsigned)w1.x;
-            if (own_prev) {
-                const ulonglong2 *s2 =
-                    reinterpret_cast<const ulonglong2 *>(p.islice + ((size_t)par * G + tid) * K);
-#pragma unroll
-                for (int q = 0; q < K / 2; ++q) {
-                    const ulonglong2 v = __ldcg(s2 + q);
-                    sl[2 * q] = v.x;
-                    sl[2 * q + 1] = v.y;
-                }
-            }
+            mine.c = (unsigned)w0.y;
+            rcnt = (int)(w0.y >> 32);
+            rq[0] = (int)(unsigned)w1.x;
+            rq[1] = (int)(unsigned)(w1.x >> 32);
+            rq[2] = (int)(unsigned)w1.y;
+            rq[3] = (int)(unsigned)(w1.y >> 32);
+            if (own_prev)
+                load_list(sl, p.islice + ((size_t)par * G + tid) * K);
+            if (ninst > 0)
+                load_list(il0, p.parts + (((size_t)pbuf * G + tid) * kMaxReq +
+                                          pend_s[sh.inst_slot[0]]) * K);
         }
-        // requests made in the previous merge are served in this one
-        const int rbuf = (int)((t + 2) % 3);
-        if (t >= 1 && tid >= kThreads - 1 - kMaxReq) {
-            if (tid == kThreads - 1) {
-                const int cnt = __ldcg(p.nreq + rbuf);
-                sh.nexec = cnt < kMaxReq ? cnt : kMaxReq;
-            } else {
-                const int s = tid - (kThreads - 1 - kMaxReq);
-                sh.exec_row[s] = __ldcg(p.req + rbuf * kMaxReq + s);
-            }
-        }
-        const Cand best = block_cand_min(mine, sh);
+        const Cand best = exchange_reduce(mine, rcnt, rq, sh);
         const long long i = (long long)(best.A & 0xffffffffull);
         const long long j = (long long)best.c;
         const float h = __uint_as_float((unsigned)(best.A >> 32));
@@ -553,38 +699,50 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                 atomicCAS(p.status, 0, kErrInternal);
             return;
         }
+        // this CTA's requests of merge t-1 now have list positions
+        {
+            const int pq = par ^ 1;
+            const int nmy = sh.nmyreq[pq];
+            if (tid < nmy) {
+                const int l = sh.myreq_l[pq][tid];
+                const int pos = sh.my_off + tid;
+                if (pos < kMaxReq)
+                    pend_s[l] = pos;
+                else
+                    pend_t[l] = -1;  // not served: the row may ask again
+            }
+        }
+        lap(ph1);
 
         // survivor of the previous merge: merge the G partial lists of its row
         if (own_prev) {
             block_topk(sl, sh);
             if (tid == 0) {
-                const int l = slot_of(prev_i);
-                store_list(ck + (size_t)l * K, sh.tko);
+                const int l = slot_of(i1);
+                cache_store(l, sh.tko);
                 const int c = list_count(sh.tko);
                 ccnt[l] = c;
                 cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
-                __stcg(p.size_g + prev_i, carried);  // deferred size write
+                __stcg(p.size_g + i1, carried);  // deferred size write
             }
         }
 
-        // refills served in the previous merge: merge the partial lists, then
-        // apply that merge's update to the row's one changed cell
-        const int ninst = sh.ninst;
+        // refills served two merges ago (in the barrier window of merge t-2):
+        // merge the partial lists, then replay merges t-2 and t-1 on the row:
+        // the served scan left out column i of merge t-2 and may have seen
+        // either value of the cells merge t-1 touched
         for (int s = 0; s < ninst; ++s) {
             const int l = sh.inst_slot[s];
             u64 L[K];
 #pragma unroll
             for (int q = 0; q < K; ++q)
-                L[q] = kNoKey;
-            if (tid < G) {
-                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(
-                    p.parts + (((size_t)(par ^ 1) * G + tid) * kMaxReq + pend_s[l]) * K);
+                L[q] = il0[q];
+            if (s > 0) {
 #pragma unroll
-                for (int q = 0; q < K / 2; ++q) {
-                    const ulonglong2 v = __ldcg(src + q);
-                    L[2 * q] = v.x;
-                    L[2 * q + 1] = v.y;
-                }
+                for (int q = 0; q < K; ++q)
+                    L[q] = kNoKey;
+                if (tid < G)
+                    load_list(L, p.parts + (((size_t)pbuf * G + tid) * kMaxReq + pend_s[l]) * K);
             }
             block_topk(L, sh);
             if (tid == 0) {
@@ -594,7 +752,8 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                     M[q] = sh.tko[q];
                 int c = list_count(M);
                 u64 B = c == K ? M[K - 1] : kNoKey;
-                const u64 x = upd[l];
+                // merge t-2: the new cell (r, i_{t-2})
+                u64 x = upd[(size_t)par * Rmax + l];
                 if (x != kNoKey && x <= B) {
                     list_insert(M, x);
                     if (c == K)
@@ -602,10 +761,32 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                     else
                         ++c;
                 }
-                store_list(ck + (size_t)l * K, M);
+                // merge t-1: column j1 left, cell (r, i1) changed
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const unsigned col = (unsigned)M[q];
+                    if (M[q] != kNoKey && (col == (unsigned)i1 || col == (unsigned)j1))
+                        M[q] = kNoKey;
+                }
+                close_holes(M);
+                c = list_count(M);
+                x = upd[(size_t)(par ^ 1) * Rmax + l];
+                if (x != kNoKey && x <= B) {
+                    list_insert(M, x);
+                    if (c == K)
+                        B = M[K - 1];
+                    else
+                        ++c;
+                }
+                cache_store(l, M);
                 ccnt[l] = c;
                 cB[l] = B;
                 pend_t[l] = -1;
+                if (c == 0 && B != kNoKey) {
+                    // every cached key left: rescan the row after the update
+                    rlist[atomicAdd(&sh.nresc, 1)] = l;
+                    pend_t[l] = -2;
+                }
             }
         }
         st_installs += ninst;
@@ -615,19 +796,18 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                 p.merges[2 * t] = (int32_t)i;
                 p.merges[2 * t + 1] = (int32_t)j;
                 p.heights[t] = h;
-                // the count buffer served two merges ago is free again
-                __stcg(p.nreq + (int)((t + 1) % 3), 0);
             }
             bitmap[j >> 5] &= ~(1u << (j & 31));  // Section 4 step 2: slot j retires
-            sh.nresc = 0;
             sh.ninst = 0;
+            sh.nmyreq[par] = 0;
         }
         int ni = 1, nj = 1;
         if (p.linkage >= 2) {
-            ni = (i == prev_i) ? carried : __ldcg(p.size_g + i);
-            nj = (j == prev_i) ? carried : __ldcg(p.size_g + j);
+            ni = (i == i1) ? carried : __ldcg(p.size_g + i);
+            nj = (j == i1) ? carried : __ldcg(p.size_g + j);
         }
         __syncthreads();
+        lap(ph2);
 
         // ---- Section 4 step 3: D(k, i+j) for every live k owned here
         float ai = 0.5f, aj = 0.5f, be = 0.0f, ga = 0.0f;
@@ -644,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
 #pragma unroll
         for (int q = 0; q < K; ++q)
             il[q] = kNoKey;
-        const int rb_now = (int)(t % 3);
+        u64 *updt = upd + (size_t)par * Rmax;
         for (int l = tid; l < R; l += kThreads) {
             const long long k = row_of(l);
             if (k >= n || k == i || k == j || !live(bitmap, k))
@@ -669,25 +849,25 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             if (k > i) {
                 // cell (i,k) belongs to the survivor row i
                 list_insert(il, make_key(s, (unsigned)k));
-                upd[l] = kNoKey;
+                updt[l] = kNoKey;
                 if (k > j)
                     continue;  // row k holds neither column i nor column j
             }
             // row k loses column j; if k < i its cell (k,i) changed as well
             u64 C[K];
+            cache_load(C, l);
 #pragma unroll
             for (int q = 0; q < K; ++q) {
-                C[q] = ck[(size_t)l * K + q];
                 const unsigned col = (unsigned)C[q];
                 if (col == (unsigned)j || (k < i && col == (unsigned)i))
                     C[q] = kNoKey;
             }
-            sort4(C);
+            close_holes(C);
             int c = list_count(C);
             u64 B = cB[l];
             if (k < i) {
                 const u64 x = make_key(s, (unsigned)i);
-                upd[l] = x;
+                updt[l] = x;
                 if (x <= B) {
                     list_insert(C, x);
                     if (c == K)
@@ -696,18 +876,20 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                         ++c;
                 }
             }
-            store_list(ck + (size_t)l * K, C);
+            cache_store(l, C);
             ccnt[l] = c;
             cB[l] = B;
-            if (c == 0) {
-                rlist[atomicAdd(&sh.nresc, 1)] = l;
-                pend_t[l] = -1;
-            } else if (c <= kRefillAt && pend_t[l] < 0) {
-                const int s2 = atomicAdd(p.nreq + rb_now, 1);
-                if (s2 < kMaxReq) {
-                    p.req[rb_now * kMaxReq + s2] = (int)k;
+            if (c == 0 && B != kNoKey) {
+                // live cells remain but none is cached: rescan (once)
+                if (pend_t[l] != -2)
+                    rlist[atomicAdd(&sh.nresc, 1)] = l;
+                pend_t[l] = -2;
+            } else if (c <= kRefillAt && B != kNoKey && pend_t[l] < 0) {
+                // (a cache that holds every live cell of its row needs no refill)
+                const int q = atomicAdd(&sh.nmyreq[par], 1);
+                if (q < kReqPerCta) {
+                    sh.myreq_l[par][q] = l;
                     pend_t[l] = (int)t;
-                    pend_s[l] = s2;
                 }
             }
         }
@@ -725,6 +907,7 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             }
         }
         __syncthreads();
+        lap(ph3);
 
         // ---- rows whose cache emptied before a refill arrived
         const int nresc = sh.nresc;
@@ -732,78 +915,116 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             const int l = rlist[q];
             block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
             if (tid == 0) {
-                store_list(ck + (size_t)l * K, sh.tko);
+                cache_store(l, sh.tko);
                 const int c = list_count(sh.tko);
                 ccnt[l] = c;
                 cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
+                pend_t[l] = -1;
             }
         }
         st_rescans += nresc;
 
-        // ---- serve the refills asked for in the previous merge: the K
-        // smallest keys of the row over this CTA's live columns, leaving out
-        // columns i and j (their cells change in this merge)
-        const int nexec = sh.nexec;
-        for (int s = 0; s < nexec; ++s) {
-            const long long r = sh.exec_row[s];
-            if (r == i || r == j || r < 0 || r >= n)
-                continue;  // the owner drops this refill
-            u64 L[K];
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                L[q] = kNoKey;
-            const long long base = tri_off(r, n) - r - 1;  // cell (r, c) at base + c
+        // ---- publish: this CTA's candidate, its refill requests and its
+        // part of the survivor row
+        {
+            Cand c = {kNoKey, 0xffffffffu};
             for (int l = tid; l < R; l += kThreads) {
-                const long long c = row_of(l);
-                if (c > r && c < n && c != i && c != j && live(bitmap, c)) {
-                    list_insert(L, make_key(__ldcg(p.D + base + c), (unsigned)c));
-                    ++st_fill_cells;
+                if (ccnt[l] > 0) {
+                    const u64 k = ck[l];
+                    Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
+                    cand_min(c, o);
+                }
+                // a refill asked for in merge t-2 was served in the barrier
+                // window of merge t-1 and is installed at merge t+1 (pend_t
+                // is negative when no refill is pending)
+                if (t >= 2 && pend_t[l] == (int)t - 2) {
+                    const int s = atomicAdd(&sh.ninst, 1);
+                    sh.inst_slot[s] = l;
                 }
             }
-            block_topk(L, sh);
-            if (tid < K / 2) {
-                ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
-                    p.parts + (((size_t)par * G + b) * kMaxReq + s) * K);
-                __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
+            block_publish(c, il, sh);
+            if (tid == 0) {
+                Cand x = sh.red[kWarps];
+                const u64 h0 = sh.tko[0];
+                if (h0 != kNoKey) {
+                    const Cand o = {(h0 & 0xffffffff00000000ull) | (u64)i, (unsigned)h0};
+                    cand_min(x, o);
+                }
+                int nq = sh.nmyreq[par];
+                nq = nq < kReqPerCta ? nq : kReqPerCta;
+                sh.nmyreq[par] = nq;
+                unsigned rr[kReqPerCta];
+#pragma unroll
+                for (int q = 0; q < kReqPerCta; ++q)
+                    rr[q] = q < nq ? (unsigned)row_of(sh.myreq_l[par][q]) : 0xffffffffu;
+                ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + (par ^ 1) * G + b);
+                __stcg(dst, make_ulonglong2(x.A, (u64)x.c | ((u64)nq << 32)));
+                __stcg(dst + 1, make_ulonglong2((u64)rr[0] | ((u64)rr[1] << 32),
+                                                (u64)rr[2] | ((u64)rr[3] << 32)));
+                sh.nresc = 0;
             }
+            publish_list(p.islice + ((size_t)(par ^ 1) * G + b) * K, sh.tko, tid);
         }
-        st_fills += nexec;
-
-        // ---- publish: this CTA's part of the survivor row and its candidate
-        block_topk(il, sh);
-        Cand c = {kNoKey, 0xffffffffu};
-        if (tid == 0 && sh.tko[0] != kNoKey) {
-            c.A = (sh.tko[0] & 0xffffffff00000000ull) | (u64)i;
-            c.c = (unsigned)sh.tko[0];
-        }
-        if (tid < K / 2) {
-            ulonglong2 *dst =
-                reinterpret_cast<ulonglong2 *>(p.islice + ((size_t)(par ^ 1) * G + b) * K);
-            __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
-        }
-        for (int l = tid; l < R; l += kThreads) {
-            if (ccnt[l] > 0) {
-                const u64 k = ck[(size_t)l * K];
-                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
-                cand_min(c, o);
-            }
-            // refills served in this merge are installed at the next one
-            // (pend_t is -1 when no refill is pending, so merge 0 has none)
-            if (t >= 1 && pend_t[l] == (int)t - 1) {
-                const int s = atomicAdd(&sh.ninst, 1);
-                sh.inst_slot[s] = l;
-            }
-        }
-        c = block_cand_min(c, sh);
-        if (tid == 0) {
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + (par ^ 1) * G + b);
-            __stcg(dst, make_ulonglong2(c.A, 0ull));
-            __stcg(dst + 1, make_ulonglong2((u64)c.c, 0ull));
-        }
-        prev_i = i;
+        lap(ph4);
+        i1 = i;
+        j1 = j;
         carried = ni + nj;
-        if (t + 2 < n && !grid_sync(p, epoch, sh))
+        if (t + 2 >= n)
+            break;  // that was the last merge
+        grid_arrive(p, epoch);
+
+        // ---- barrier window: serve the refills asked for in the previous
+        // merge, one warp per row: the K smallest keys of the row over this
+        // CTA's live columns, leaving out column i (its cells were rewritten
+        // by other CTAs in this merge and may not be visible yet).  The
+        // lists are read two merges later, after the next barrier.
+        {
+            const int nexec = sh.nexec;
+            const int sbuf = (int)(t % 3);
+            for (int s = warp; s < nexec; s += kWarps) {
+                const long long r = sh.exec_row[s];
+                if (r < 0 || r >= n || r == i || r == j)
+                    continue;  // the owner drops this refill
+                u64 L[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q)
+                    L[q] = kNoKey;
+                const long long base = tri_off(r, n) - r - 1;  // cell (r, c) at base + c
+                long long cnt = 0;
+                for (long long qb0 = 0; qb0 < my_blocks; qb0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const long long qb = qb0 + u;
+                        const long long c = ((long long)b + (long long)G * qb) * kRowBlock + lane;
+                        v[u] = -1.0f;  // marks "no cell"; real cells are >= 0
+                        if (qb < my_blocks && c > r && c < n && c != i && live(bitmap, c))
+                            v[u] = __ldcg(p.D + base + c);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        if (v[u] >= 0.0f) {
+                            const long long c = ((long long)b + (long long)G * (qb0 + u)) * kRowBlock + lane;
+                            list_insert(L, make_key(v[u], (unsigned)c));
+                            ++cnt;
+                        }
+                    }
+                }
+                st_fill_cells += cnt;
+                u64 w[K];
+                warp_topk(L, w);
+                if (lane < K / 2) {
+                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
+                        p.parts + (((size_t)sbuf * G + b) * kMaxReq + s) * K);
+                    __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
+                }
+            }
+            st_fills += nexec;
+        }
+        lap(ph5);
+        if (!grid_wait(p, epoch, sh))
             return;
+        lap(ph0);
     }
 
     if (p.stats) {
@@ -818,6 +1039,14 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                 S[3] = (u64)G;
                 S[4] = (u64)st_fills;
             }
+            if (p.timing) {
+                atomicAdd(S + 8, ph0);
+                atomicAdd(S + 9, ph1);
+                atomicAdd(S + 10, ph2);
+                atomicAdd(S + 11, ph3);
+                atomicAdd(S + 12, ph4);
+                atomicAdd(S + 13, ph5);
+            }
         }
     }
 }
@@ -829,7 +1058,7 @@ size_t merge_smem_bytes(long long n, int G)
     const long long nb = (n + kRowBlock - 1) / kRowBlock;
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * (8 * K + 8 + 8 + 4 * 5));
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * (8 * K + 8 + 16 + 4 * 5));
 }
 
 bool merge_config_ok(long long n, int G, int num_sms)

@@ -23,10 +23,10 @@
 namespace {
 
 // Largest n this entry point accepts and the scratch that serves it: cluster
-// sizes 4n, per-CTA candidate and partial-list records (about 2 KB per CTA
+// sizes 4n, per-CTA candidate and partial-list records (about 3.2 KB per CTA
 // of a full-device grid), request, barrier, status and stats words.
 constexpr long long kNoAllocMaxN = LW_NOALLOC_MAX_N;
-constexpr size_t kScratchBytes = 512 * 1024;
+constexpr size_t kScratchBytes = 1024 * 1024;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -112,16 +112,15 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
     p.cand = reinterpret_cast<lw::Rec *>(ws + L.cand);
     p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
     p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
-    p.req = reinterpret_cast<int *>(ws + L.req);
-    p.nreq = reinterpret_cast<int *>(ws + L.nreq);
     p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
     p.status = reinterpret_cast<int *>(ws + L.status);
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = 5000ull * 1000000ull;
     p.skip_arrive_cta = -1;
+    p.timing = 0;
 
-    // the scratch keeps the previous call's contents: the request counts,
-    // barrier, status and stats words must start at zero
+    // the scratch keeps the previous call's contents: the barrier,
+    // status and stats words must start at zero
     if (cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, stream) != cudaSuccess ||
         lw::launch_merge(p, stream) != cudaSuccess) {
         cudaGetLastError();

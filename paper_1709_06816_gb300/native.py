@@ -126,12 +126,17 @@ def lw_wait(ctx: int) -> None:
 
 def lw_get_stats(ctx: int) -> dict:
     lib = load()
-    a = (ctypes.c_int64 * 8)()
-    s = lib.lw_get_stats(ctx, a, 8)
+    a = (ctypes.c_int64 * 16)()
+    s = lib.lw_get_stats(ctx, a, 16)
     if s != 0:
         raise LwError(s, "lw_get_stats")
-    return {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3],
-            "refills": a[4], "refill_cells": a[5], "installs": a[6]}
+    out = {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3],
+           "refills": a[4], "refill_cells": a[5], "installs": a[6]}
+    if any(a[8:14]):
+        G = max(1, a[3])
+        names = ("barrier", "exchange", "installs", "update", "publish", "refill")
+        out["phase_ms"] = {nm: a[8 + q] / G / 1e6 for q, nm in enumerate(names)}
+    return out
 
 
 def lw_set_option(ctx: int, option: int, value: int) -> None:
@@ -194,6 +199,9 @@ class Context:
 
     def set_grid(self, G: int):
         lw_set_option(self.handle, LW_OPT_GRID, G)
+
+    def set_phase_timing(self, on: bool = True):
+        lw_set_option(self.handle, 4, 1 if on else 0)
 
     def set_timeout_ms(self, ms: int):
         lw_set_option(self.handle, LW_OPT_TIMEOUT_MS, ms)
