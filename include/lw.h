@@ -145,10 +145,19 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *                     so the other CTAs' bounded waits run out and the call
  *                     reports LW_ERR_TIMEOUT with the context still usable;
  *                     -1 switches it off (the default);
- *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..13]).
+ *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..13]);
+ *   LW_OPT_BATCH_SPLIT  largest n a batch runs on a single CTA (0: the
+ *                     largest that fits one CTA's shared memory); larger
+ *                     jobs of a batch run over the whole device.
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
-enum { LW_OPT_GRID = 1, LW_OPT_TIMEOUT_MS = 2, LW_OPT_TEST_SKIP_ARRIVE = 3, LW_OPT_PHASE_TIMES = 4 };
+enum {
+    LW_OPT_GRID = 1,
+    LW_OPT_TIMEOUT_MS = 2,
+    LW_OPT_TEST_SKIP_ARRIVE = 3,
+    LW_OPT_PHASE_TIMES = 4,
+    LW_OPT_BATCH_SPLIT = 5
+};
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
 /*
@@ -181,6 +190,53 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 #define LW_NOALLOC_MAX_N 16384
 lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int32_t *merges_out,
                              float *heights_out, void *cuda_stream);
+
+/*
+ * Batches: many independent clusterings in one persistent launch.
+ *
+ * A job whose n is at most the split size (LW_OPT_BATCH_SPLIT, default the
+ * largest n one CTA's shared memory can hold) runs entirely on one CTA: the
+ * batch kernel keeps one CTA per SM slot busy, each CTA taking the next job
+ * from a device work queue until the queue is empty, so thousands of small
+ * jobs cost one launch.  Larger jobs run one after another over the whole
+ * device, as lw_cluster would run them.  Results are bit-identical to
+ * lw_cluster on each job alone.
+ */
+typedef struct lw_job {
+    float *dist;          /* DEVICE packed upper triangle, n(n-1)/2 floats, overwritten */
+    int64_t n;            /* 1 <= n <= LW_MAX_N */
+    int32_t linkage;      /* lw_linkage */
+    int32_t status;       /* out: lw_status of this job (written by lw_batch_wait) */
+    int32_t *merges_out;  /* DEVICE int32[2(n-1)] */
+    float *heights_out;   /* DEVICE float[n-1] */
+} lw_job;
+
+typedef struct lw_batch lw_batch;
+
+/*
+ * lw_batch_create -- plan a batch: checks every job (LW_ERR_INVALID_ARG for a
+ * bad n, linkage or non-device pointer, with the job's index in
+ * lw_last_error), copies the job table to the device, sizes the per-CTA
+ * scratch and records the small-job launch as a CUDA graph on the context's
+ * stream.  The plan can be run many times; the jobs' buffers must stay valid
+ * until lw_batch_destroy.  Nothing runs yet.
+ */
+lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_batch **out);
+
+/* lw_batch_run -- queue one run of the plan on the context's stream (graph
+ * replay, then the large jobs); returns without waiting. */
+lw_status lw_batch_run(lw_batch *batch);
+
+/* lw_batch_wait -- wait for the last run; writes each job's status into
+ * jobs[q].status when jobs is not NULL (same order as at creation) and
+ * returns LW_OK if every job succeeded, else the first failing status. */
+lw_status lw_batch_wait(lw_batch *batch, lw_job *jobs);
+
+/* lw_batch_destroy -- free the plan (NULL is a no-op). */
+void lw_batch_destroy(lw_batch *batch);
+
+/* lw_cluster_batch -- create, run, wait and destroy in one blocking call. */
+lw_status lw_cluster_batch(lw_ctx *ctx, lw_job *jobs, int32_t njobs);
 
 /* lw_status_string -- static text for a status code. */
 const char *lw_status_string(lw_status s);

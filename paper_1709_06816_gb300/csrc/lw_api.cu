@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 struct lw_ctx {
     int device = 0;
@@ -23,6 +24,7 @@ struct lw_ctx {
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
     int phase_timing = 0;
+    long long batch_split = 0;  // 0: largest n one CTA can hold
 
     // device workspace
     void *ws = nullptr;
@@ -412,9 +414,278 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
     case LW_OPT_PHASE_TIMES:
         ctx->phase_timing = value != 0;
         return LW_OK;
+    case LW_OPT_BATCH_SPLIT:
+        if (value < 0)
+            return LW_ERR_INVALID_ARG;
+        ctx->batch_split = value;
+        return LW_OK;
     default:
         return LW_ERR_INVALID_ARG;
     }
+}
+
+}  // extern "C"
+
+struct lw_batch {
+    lw_ctx *ctx = nullptr;
+    int njobs = 0;
+    std::vector<lw_job> jobs;        // host copy of the table
+    std::vector<int> small_idx;      // jobs run one per CTA
+    std::vector<int> big_idx;        // jobs run over the whole device
+    lw::BatchJob *d_jobs = nullptr;  // small-job table
+    int *d_status = nullptr;         // [small] statuses, then [big] statuses
+    int *d_queue = nullptr;
+    long long *d_merges = nullptr;
+    char *d_ws = nullptr;
+    int grid = 0;
+    long long n_max = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Largest n whose one-CTA shared memory fits (and lets at least one CTA run).
+long long batch_auto_split()
+{
+    long long lo = 2, hi = 1 << 16;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if (lw::batch_ctas_per_sm(mid) >= 1)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+void batch_free(lw_batch *b)
+{
+    if (!b)
+        return;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_status);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_merges);
+    cudaFree(b->d_ws);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_batch **out)
+{
+    if (!ctx || !out || njobs < 0 || (njobs > 0 && !jobs))
+        return LW_ERR_INVALID_ARG;
+    *out = nullptr;
+    BusyGuard guard(ctx);
+    if (!guard.ok) {
+        set_err(ctx, "context busy");
+        return LW_ERR_BUSY;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaSetDevice");
+    lw_batch *b = new (std::nothrow) lw_batch;
+    if (!b)
+        return LW_ERR_OOM;
+    b->ctx = ctx;
+    b->njobs = njobs;
+    b->jobs.assign(jobs, jobs + njobs);
+    const long long split = ctx->batch_split > 0 ? ctx->batch_split : batch_auto_split();
+    long long big_n = 0;
+    for (int q = 0; q < njobs; ++q) {
+        const lw_job &J = jobs[q];
+        if (J.n < 1 || J.n > LW_MAX_N || J.linkage < LW_SINGLE || J.linkage > LW_WARD ||
+            (J.n > 1 && (!is_device_ptr(J.dist) || !is_device_ptr(J.merges_out) ||
+                         !is_device_ptr(J.heights_out)))) {
+            set_err(ctx, "job %d: bad n, linkage or a pointer that is not device memory", q);
+            batch_free(b);
+            return LW_ERR_INVALID_ARG;
+        }
+        if (J.n <= split) {
+            b->small_idx.push_back(q);
+            b->n_max = J.n > b->n_max ? J.n : b->n_max;
+        } else {
+            b->big_idx.push_back(q);
+            big_n = J.n > big_n ? J.n : big_n;
+        }
+    }
+    const size_t nsmall = b->small_idx.size(), nbig = b->big_idx.size();
+    lw_status st = LW_OK;
+    auto alloc = [&](void **pp, size_t bytes, const char *what) {
+        if (st != LW_OK)
+            return;
+        cudaError_t ee = cudaMalloc(pp, bytes < 16 ? 16 : bytes);
+        if (ee != cudaSuccess) {
+            cudaGetLastError();
+            set_err(ctx, "cudaMalloc(%zu) for %s failed", bytes, what);
+            st = LW_ERR_OOM;
+        }
+    };
+    alloc((void **)&b->d_status, sizeof(int) * (nsmall + nbig), "batch statuses");
+    alloc((void **)&b->d_queue, sizeof(int), "batch queue");
+    alloc((void **)&b->d_merges, sizeof(long long), "batch counter");
+    if (nsmall > 0) {
+        std::vector<lw::BatchJob> table(nsmall);
+        for (size_t q = 0; q < nsmall; ++q) {
+            const lw_job &J = jobs[b->small_idx[q]];
+            table[q].D = J.dist;
+            table[q].n = J.n;
+            table[q].linkage = J.linkage;
+            table[q].pad = 0;
+            table[q].merges = J.merges_out;
+            table[q].heights = J.heights_out;
+        }
+        const int per_sm = lw::batch_ctas_per_sm(b->n_max < 2 ? 2 : b->n_max);
+        if (per_sm < 1 && st == LW_OK) {
+            set_err(ctx, "batch jobs of n=%lld do not fit one CTA", b->n_max);
+            st = LW_ERR_INVALID_ARG;
+        }
+        b->grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+        if ((size_t)b->grid > nsmall)
+            b->grid = (int)nsmall;
+        const lw::WorkspaceLayout L = lw::workspace_layout(b->n_max, 1);
+        alloc((void **)&b->d_jobs, sizeof(lw::BatchJob) * nsmall, "batch table");
+        alloc((void **)&b->d_ws, L.total * (size_t)b->grid, "batch slots");
+        if (st == LW_OK &&
+            (e = cudaMemcpy(b->d_jobs, table.data(), sizeof(lw::BatchJob) * nsmall,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            st = cuda_fail(ctx, e, "cudaMemcpy(batch table)");
+        // record the small-job launch as a graph: reset the queue, run the batch kernel
+        if (st == LW_OK) {
+            lw::BatchParams bp;
+            bp.jobs = b->d_jobs;
+            bp.njobs = (int)nsmall;
+            bp.n_max = b->n_max;
+            bp.queue = b->d_queue;
+            bp.ws = b->d_ws;
+            bp.job_status = b->d_status;
+            bp.merges_done = b->d_merges;
+            bp.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
+            e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaMemsetAsync(b->d_queue, 0, sizeof(int), ctx->stream);
+                cudaMemsetAsync(b->d_merges, 0, sizeof(long long), ctx->stream);
+                cudaError_t el = lw::launch_batch(bp, b->grid, ctx->stream);
+                e = cudaStreamEndCapture(ctx->stream, &b->graph);
+                if (e == cudaSuccess)
+                    e = el;
+            }
+            if (e == cudaSuccess)
+                e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (e != cudaSuccess)
+                st = cuda_fail(ctx, e, "batch graph capture");
+        }
+    }
+    if (st == LW_OK && nbig > 0) {
+        // size the context's workspace now so that runs never allocate
+        const int G = choose_grid(ctx, big_n);
+        if (G <= 0) {
+            set_err(ctx, "n=%lld does not fit a co-resident grid on this device", big_n);
+            st = LW_ERR_INVALID_ARG;
+        } else {
+            st = ensure(ctx, &ctx->ws, &ctx->ws_cap, lw::workspace_layout(big_n, ctx->num_sms).total,
+                        "workspace");
+        }
+    }
+    if (st != LW_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return LW_OK;
+}
+
+lw_status lw_batch_run(lw_batch *b)
+{
+    if (!b)
+        return LW_ERR_INVALID_ARG;
+    lw_ctx *ctx = b->ctx;
+    BusyGuard guard(ctx);
+    if (!guard.ok) {
+        set_err(ctx, "context busy");
+        return LW_ERR_BUSY;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaSetDevice");
+    if (b->exec && (e = cudaGraphLaunch(b->exec, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaGraphLaunch");
+    const size_t nsmall = b->small_idx.size();
+    for (size_t q = 0; q < b->big_idx.size(); ++q) {
+        const lw_job &J = b->jobs[b->big_idx[q]];
+        lw_status s = enqueue(ctx, J.dist, J.n, J.linkage, J.merges_out, J.heights_out);
+        if (s != LW_OK)
+            return s;
+        if ((e = cudaMemcpyAsync(b->d_status + nsmall + q, ctx->d_status, sizeof(int),
+                                 cudaMemcpyDeviceToDevice, ctx->stream)) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMemcpyAsync(job status)");
+    }
+    return LW_OK;
+}
+
+lw_status lw_batch_wait(lw_batch *b, lw_job *jobs)
+{
+    if (!b)
+        return LW_ERR_INVALID_ARG;
+    lw_ctx *ctx = b->ctx;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    const size_t nsmall = b->small_idx.size(), nbig = b->big_idx.size();
+    std::vector<int> st(nsmall + nbig, 0);
+    if (!st.empty() &&
+        (e = cudaMemcpy(st.data(), b->d_status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemcpy(job statuses)");
+    lw_status first = LW_OK;
+    for (size_t q = 0; q < st.size(); ++q) {
+        const int idx = q < nsmall ? b->small_idx[q] : b->big_idx[q - nsmall];
+        lw_status js = LW_OK;
+        switch (st[q]) {
+        case 0: js = LW_OK; break;
+        case lw::kErrInput: js = LW_ERR_INVALID_INPUT; break;
+        case lw::kErrTimeout: js = LW_ERR_TIMEOUT; break;
+        default: js = LW_ERR_CUDA; break;
+        }
+        if (jobs)
+            jobs[idx].status = js;
+        if (js != LW_OK && first == LW_OK) {
+            first = js;
+            set_err(ctx, "job %d: %s", idx, lw_status_string(js));
+        }
+    }
+    return first;
+}
+
+void lw_batch_destroy(lw_batch *b)
+{
+    if (!b)
+        return;
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    batch_free(b);
+}
+
+lw_status lw_cluster_batch(lw_ctx *ctx, lw_job *jobs, int32_t njobs)
+{
+    lw_batch *b = nullptr;
+    lw_status s = lw_batch_create(ctx, jobs, njobs, &b);
+    if (s != LW_OK)
+        return s;
+    s = lw_batch_run(b);
+    if (s == LW_OK)
+        s = lw_batch_wait(b, jobs);
+    lw_batch_destroy(b);
+    return s;
 }
 
 const char *lw_status_string(lw_status s)

@@ -59,7 +59,7 @@ struct WorkspaceLayout {
     size_t size, cand, islice, parts, zero, bar, status, stats, total;
 };
 
-inline WorkspaceLayout workspace_layout(long long n, int G)
+__host__ __device__ inline WorkspaceLayout workspace_layout(long long n, int G)
 {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     WorkspaceLayout L;
@@ -76,11 +76,37 @@ inline WorkspaceLayout workspace_layout(long long n, int G)
     return L;
 }
 
+// One job of a batch (device table entry).
+struct BatchJob {
+    float *D;                      // packed upper triangle (device), rewritten in place
+    long long n;
+    int linkage;
+    int pad;
+    int32_t *merges;               // [2(n-1)] device
+    float *heights;                // [n-1]    device
+};
+
+struct BatchParams {
+    const BatchJob *jobs;          // [njobs] device
+    int njobs;
+    long long n_max;               // largest n in the table (sizes shared memory and slots)
+    int *queue;                    // next job to take (zero at launch)
+    char *ws;                      // one workspace slot per CTA, workspace_layout(n_max, 1)
+    int *job_status;               // [njobs] lw_status of each job
+    long long *merges_done;        // total merges performed (optional)
+    unsigned long long timeout_ns;
+};
+
 // Bytes of dynamic shared memory the merge kernel needs for (n, G).
 size_t merge_smem_bytes(long long n, int G);
 // True if a grid of G CTAs for n objects fits co-resident on the current device.
 bool merge_config_ok(long long n, int G, int num_sms);
 // Launch the persistent kernel cooperatively on `stream`.
 cudaError_t launch_merge(const MergeParams &p, cudaStream_t stream);
+// CTAs of the batch kernel that fit on one SM for jobs up to n_max.
+int batch_ctas_per_sm(long long n_max);
+// Launch the batch kernel (grid CTAs, one workspace slot each) on `stream`;
+// call batch_ctas_per_sm(bp.n_max) first (it sets the shared-memory limit).
+cudaError_t launch_batch(const BatchParams &bp, int grid, cudaStream_t stream);
 
 }  // namespace lw

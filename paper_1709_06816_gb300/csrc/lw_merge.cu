@@ -218,7 +218,7 @@ struct Shared {
 // (deterministic, the same in every CTA), cut at kMaxReq.  Thread t holds
 // CTA t's record (cnt requests in rq).  Sets sh.exec_row, sh.nexec and
 // sh.my_off (the position of this CTA's first request).
-__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], Shared &sh)
+__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], int b, Shared &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = cnt;
@@ -243,7 +243,7 @@ __device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], Sh
         if (q < cnt && off0 + q < kMaxReq)
             sh.exec_row[off0 + q] = rq[q];
     }
-    if ((int)threadIdx.x == (int)blockIdx.x)
+    if ((int)threadIdx.x == b)
         sh.my_off = off0;
     if (warp == 0) {
         Cand w = {kNoKey, 0xffffffffu};
@@ -507,14 +507,13 @@ __device__ __forceinline__ void publish_list(u64 *dst, const u64 *src, int tid)
         __stcg(reinterpret_cast<ulonglong2 *>(dst) + tid, make_ulonglong2(src[2 * tid], src[2 * tid + 1]));
 }
 
-__global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
+// All n - 1 merges of one job, run by CTA b of the job's G CTAs (every CTA
+// of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
+// bytes of dynamic shared memory.
+__device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared &sh)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
-
     const long long n = p.n;
     const int G = p.G;
-    const int b = blockIdx.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const long long nb = (n + kRowBlock - 1) / kRowBlock;      // row blocks
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
                 load_list(il0, p.parts + (((size_t)pbuf * G + tid) * kMaxReq +
                                           pend_s[sh.inst_slot[0]]) * K);
         }
-        const Cand best = exchange_reduce(mine, rcnt, rq, sh);
+        const Cand best = exchange_reduce(mine, rcnt, rq, b, sh);
         const long long i = (long long)(best.A & 0xffffffffull);
         const long long j = (long long)best.c;
         const float h = __uint_as_float((unsigned)(best.A >> 32));
@@ -923,6 +922,8 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
             }
         }
         st_rescans += nresc;
+        if (nresc > 0)
+            __syncthreads();  // the rescanned caches (written by thread 0) before anyone reads them
 
         // ---- publish: this CTA's candidate, its refill requests and its
         // part of the survivor row
@@ -1051,6 +1052,67 @@ __global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
     }
 }
 
+__global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Shared sh;
+    merge_job(p, blockIdx.x, smem_raw, sh);
+}
+
+// Many independent jobs in one persistent launch: each CTA takes the next job
+// from a queue (atomicAdd on a counter) and runs all its merges alone (a
+// one-CTA job needs no grid barrier), then takes another, until the queue is
+// empty.  CTA c keeps its scratch in workspace slot c.
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Shared sh;
+    __shared__ int job;
+    const WorkspaceLayout L = workspace_layout(bp.n_max, 1);
+    char *ws = bp.ws + (size_t)blockIdx.x * L.total;
+    long long merges_done = 0;
+    while (true) {
+        if (threadIdx.x == 0)
+            job = atomicAdd(bp.queue, 1);
+        __syncthreads();
+        const int jb = job;
+        if (jb >= bp.njobs)
+            break;
+        const BatchJob J = bp.jobs[jb];
+        MergeParams p;
+        p.D = J.D;
+        p.n = J.n;
+        p.linkage = J.linkage;
+        p.G = 1;
+        p.aligned16 = ((uintptr_t)J.D & 15u) == 0;
+        p.merges = J.merges;
+        p.heights = J.heights;
+        p.size_g = reinterpret_cast<int *>(ws + L.size);
+        p.cand = reinterpret_cast<Rec *>(ws + L.cand);
+        p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
+        p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
+        p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
+        p.status = reinterpret_cast<int *>(ws + L.status);
+        p.stats = nullptr;
+        p.timeout_ns = bp.timeout_ns;
+        p.skip_arrive_cta = -1;
+        p.timing = 0;
+        // the slot keeps the previous job's words: clear the ones that must start at zero
+        for (size_t q = threadIdx.x; q < (L.total - L.zero) / 4; q += kThreads)
+            reinterpret_cast<int *>(ws + L.zero)[q] = 0;
+        __syncthreads();
+        if (J.n > 1)
+            merge_job(p, 0, smem_raw, sh);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bp.job_status[jb] = J.n > 1 ? __ldcg(p.status) : 0;
+            merges_done += J.n > 1 ? J.n - 1 : 0;
+        }
+    }
+    if (threadIdx.x == 0 && bp.merges_done)
+        atomicAdd(reinterpret_cast<unsigned long long *>(bp.merges_done), (unsigned long long)merges_done);
+}
+
 }  // namespace
 
 size_t merge_smem_bytes(long long n, int G)
@@ -1082,6 +1144,28 @@ bool merge_config_ok(long long n, int G, int num_sms)
         cudaSuccess)
         return false;
     return per_sm >= 1;
+}
+
+int batch_ctas_per_sm(long long n_max)
+{
+    const size_t smem = merge_smem_bytes(n_max, 1);
+    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+cudaError_t launch_batch(const BatchParams &bp, int grid, cudaStream_t stream)
+{
+    // batch_ctas_per_sm(bp.n_max) has set the kernel's shared-memory limit
+    // (this launch may be recorded into a graph, where no attribute is set)
+    const size_t smem = merge_smem_bytes(bp.n_max, 1);
+    batch_kernel<<<grid, kThreads, smem, stream>>>(bp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const MergeParams &p, cudaStream_t stream)

@@ -27,7 +27,16 @@ STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW
 # every symbol include/lw.h declares
 EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
            "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy",
-           "lw_cluster_noalloc")
+           "lw_batch_create", "lw_batch_run", "lw_batch_wait", "lw_batch_destroy",
+           "lw_cluster_batch", "lw_cluster_noalloc")
+LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT = 4, 5
+
+
+class LwJob(ctypes.Structure):
+    """struct lw_job of include/lw.h."""
+    _fields_ = [("dist", ctypes.c_void_p), ("n", ctypes.c_int64), ("linkage", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("merges_out", ctypes.c_void_p),
+                ("heights_out", ctypes.c_void_p)]
 LW_NOALLOC_MAX_N = 16384
 
 _lib = None
@@ -72,6 +81,17 @@ def load(path: str = LIB_PATH):
         lib.lw_destroy.restype = None
         lib.lw_cluster_noalloc.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
         lib.lw_cluster_noalloc.restype = ctypes.c_int
+        jp = ctypes.POINTER(LwJob)
+        lib.lw_batch_create.argtypes = [vp, jp, ctypes.c_int32, ctypes.POINTER(vp)]
+        lib.lw_batch_create.restype = ctypes.c_int
+        lib.lw_batch_run.argtypes = [vp]
+        lib.lw_batch_run.restype = ctypes.c_int
+        lib.lw_batch_wait.argtypes = [vp, jp]
+        lib.lw_batch_wait.restype = ctypes.c_int
+        lib.lw_batch_destroy.argtypes = [vp]
+        lib.lw_batch_destroy.restype = None
+        lib.lw_cluster_batch.argtypes = [vp, jp, ctypes.c_int32]
+        lib.lw_cluster_batch.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -158,6 +178,38 @@ def lw_cluster_noalloc(dist, n: int, linkage: int, merges_out, heights_out, stre
         raise LwError(s, "lw_cluster_noalloc")
 
 
+def lw_batch_create(ctx: int, jobs) -> int:
+    """jobs: a ctypes array of LwJob.  Returns the plan handle."""
+    lib = load()
+    h = ctypes.c_void_p()
+    s = lib.lw_batch_create(ctx, jobs, len(jobs), ctypes.byref(h))
+    if s != 0:
+        raise LwError(s, lib.lw_last_error(ctx).decode())
+    return h.value
+
+
+def lw_batch_run(batch: int, ctx: int = 0) -> None:
+    lib = load()
+    s = lib.lw_batch_run(batch)
+    if s != 0:
+        raise LwError(s, lib.lw_last_error(ctx).decode() if ctx else "lw_batch_run")
+
+
+def lw_batch_wait(batch: int, jobs=None) -> int:
+    """Waits; fills jobs[q].status; returns the first failing status (0 = all ok)."""
+    return int(load().lw_batch_wait(batch, jobs))
+
+
+def lw_batch_destroy(batch: int) -> None:
+    if batch:
+        load().lw_batch_destroy(batch)
+
+
+def lw_cluster_batch(ctx: int, jobs) -> int:
+    """Blocking batch; fills jobs[q].status; returns the first failing status."""
+    return int(load().lw_cluster_batch(ctx, jobs, len(jobs)))
+
+
 def lw_status_string(status: int) -> str:
     return load().lw_status_string(int(status)).decode()
 
@@ -202,6 +254,36 @@ class Context:
 
     def set_phase_timing(self, on: bool = True):
         lw_set_option(self.handle, 4, 1 if on else 0)
+
+    def set_batch_split(self, n: int):
+        lw_set_option(self.handle, LW_OPT_BATCH_SPLIT, n)
+
+    def make_jobs(self, mats, ns, linkages):
+        """Job table for device matrices; allocates the device outputs.
+        Returns (ctypes LwJob array, list of (merges, heights) tensors)."""
+        import torch
+        jobs = (LwJob * len(mats))()
+        outs = []
+        for q, (D, n, link) in enumerate(zip(mats, ns, linkages)):
+            if isinstance(link, str):
+                link = LINKAGES[link]
+            self._check_matrix(D, n)
+            m = torch.empty((max(n - 1, 0), 2), dtype=torch.int32, device=D.device)
+            h = torch.empty(max(n - 1, 0), dtype=torch.float32, device=D.device)
+            jobs[q].dist = D.data_ptr() if D.numel() else 0
+            jobs[q].n = n
+            jobs[q].linkage = link
+            jobs[q].status = -1
+            jobs[q].merges_out = m.data_ptr() if m.numel() else 0
+            jobs[q].heights_out = h.data_ptr() if h.numel() else 0
+            outs.append((m, h))
+        return jobs, outs
+
+    def cluster_batch(self, mats, ns, linkages):
+        """Cluster many device matrices in one batch.  Returns (outs, statuses)."""
+        jobs, outs = self.make_jobs(mats, ns, linkages)
+        lw_cluster_batch(self.handle, jobs)
+        return outs, [jobs[q].status for q in range(len(mats))]
 
     def set_timeout_ms(self, ms: int):
         lw_set_option(self.handle, LW_OPT_TIMEOUT_MS, ms)
