@@ -287,6 +287,9 @@ def run_ours(args, world, rank, local):
                           f"work sum(m_t): {info['est_total_s']:.1f} s")}
 
     ctx.close()
+    del work
+    torch.cuda.empty_cache()
+    batched = None if args.no_batched else run_batched(args, local)
     peak, peak_kind = peaks()
     alg, alg_note = algorithmic_bytes(n, LINKAGE, work_counts(args.workload, LINKAGE))
     k_avg_ms = sum(kernel_ms) / len(kernel_ms)
@@ -323,9 +326,87 @@ def run_ours(args, world, rank, local):
         "gpu_launches": args.steps,
         "clocks": clocks,
         "counters": stats,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_batched(args, local, plain_sample: int = 256):
+    """The batched workload: 4096 independent jobs (n log-uniform in [64, 2048],
+    linkage uniform over the four, R^16 Gaussian mixtures) through one batch
+    plan (one persistent launch, work queue, CUDA graph), against the same jobs
+    through one lw_cluster call each on one stream (timed on a sample)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1709_06816_gb300 import Context, native
+
+    dev = f"cuda:{local}"
+    specs = synth.batch_jobs()
+    sizes = [n * (n - 1) // 2 for n, _, _ in specs]
+    offs = np.zeros(len(specs) + 1, dtype=np.int64)
+    for q, c in enumerate(sizes):
+        offs[q + 1] = offs[q] + ((c + 3) // 4) * 4  # 16-byte aligned starts
+    pristine = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
+    for q, spec in enumerate(specs):
+        pristine[int(offs[q]):int(offs[q]) + sizes[q]] = synth.job_matrix(spec, q, device=dev)
+    work = pristine.clone()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream=stream)
+    mats = [work[int(offs[q]):int(offs[q]) + sizes[q]] for q in range(len(specs))]
+    table, outs = ctx.make_jobs(mats, [n for n, _, _ in specs], [l for _, l, _ in specs])
+    plan = native.lw_batch_create(ctx.handle, table)
+    total_merges = sum(n - 1 for n, _, _ in specs)
+    times = []
+    try:
+        for k in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                work.copy_(pristine)
+                e0.record(stream)
+            native.lw_batch_run(plan, ctx.handle)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            rc = native.lw_batch_wait(plan, table)
+            if rc != 0:
+                raise RuntimeError(f"batch failed: {native.lw_status_string(rc)}")
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    finally:
+        native.lw_batch_destroy(plan)
+    batch_ms = statistics.median(times)
+    # plain path: one lw_cluster launch per job, same stream, a sample of the jobs
+    pick = list(range(0, len(specs), max(1, len(specs) // plain_sample)))[:plain_sample]
+    with torch.cuda.stream(stream):
+        work.copy_(pristine)
+    torch.cuda.synchronize()
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        pe0.record(stream)
+    for q in pick:
+        m, h = outs[q]
+        ctx.cluster_async(mats[q], specs[q][0], specs[q][1], m, h)
+    with torch.cuda.stream(stream):
+        pe1.record(stream)
+    ctx.wait()
+    plain_ms = pe0.elapsed_time(pe1)
+    ctx.close()
+    jobs_per_s = len(specs) / (batch_ms * 1e-3)
+    plain_jobs_per_s = len(pick) / (plain_ms * 1e-3)
+    return {
+        "metric": "jobs/s (4096 independent jobs, n log-uniform in [64,2048], mixed linkage)",
+        "value": jobs_per_s, "unit": "jobs/s", "ms_per_batch": batch_ms,
+        "merges_per_s": total_merges / (batch_ms * 1e-3), "n_jobs": len(specs),
+        "total_merges": total_merges, "matrix_bytes": 4 * int(sum(sizes)),
+        "plain_jobs_per_s": plain_jobs_per_s, "plain_sample_jobs": len(pick),
+        "speedup_vs_plain": jobs_per_s / plain_jobs_per_s,
+        "step": "restore all matrices (one device copy) + one batch-plan run (CUDA graph: "
+                "queue reset + persistent CTA-per-job kernel)",
+    }
 
 
 def run_reference(args, world, rank, local):
@@ -385,6 +466,7 @@ def main(argv=None):
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload name (profiling uses smaller conformer<N> cases)")
     args = ap.parse_args(argv)
