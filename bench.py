@@ -290,6 +290,8 @@ def run_ours(args, world, rank, local):
     del work
     torch.cuda.empty_cache()
     batched = None if args.no_batched else run_batched(args, local)
+    torch.cuda.empty_cache()
+    serving = None if args.no_serving else run_serving(args, local)
     peak, peak_kind = peaks()
     alg, alg_note = algorithmic_bytes(n, LINKAGE, work_counts(args.workload, LINKAGE))
     k_avg_ms = sum(kernel_ms) / len(kernel_ms)
@@ -327,6 +329,7 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "counters": stats,
         "batched": batched,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -409,6 +412,64 @@ def run_batched(args, local, plain_sample: int = 256):
     }
 
 
+def run_serving(args, local, n_requests: int = 2000, bank_size: int = 48):
+    """The serving workload: a Poisson stream (mean 200 requests/s) of
+    clustering requests, n log-uniform in [256, 32768], linkage uniform over
+    the four, R^16 Gaussian-mixture distances, through a server with a
+    120 GB pool.  Matrices come from a bank of bank_size requests of the same
+    stream, generated on the device beforehand (request q uses bank entry
+    q mod bank_size, with that entry's n); latency runs from submission (the
+    matrix is ready on the device) to completion."""
+    import time as _time
+
+    import torch
+
+    import synth
+    from paper_1709_06816_gb300.native import Server
+
+    dev = f"cuda:{local}"
+    stream_specs = synth.serve_requests(n_requests)
+    bank = []
+    for (_, n, link, K, q) in stream_specs[:bank_size]:
+        rng_seed = [4, q]
+        pts = synth.gmm_points(__import__("numpy").random.default_rng(rng_seed), n, 16, K, 10.0, 1.0)
+        bank.append((synth.packed_distances(pts, device=dev), n, link))
+    outs = []
+    for q in range(n_requests):
+        D, n, link = bank[q % bank_size]
+        outs.append((torch.empty((n - 1, 2), dtype=torch.int32, device=dev),
+                     torch.empty(n - 1, dtype=torch.float32, device=dev)))
+    torch.cuda.synchronize()
+    srv = Server(local, budget_bytes=120 * 10**9, lanes=48)
+    try:
+        t0 = _time.perf_counter()
+        for q, (arrival, _, _, _, _) in enumerate(stream_specs):
+            wait = arrival - (_time.perf_counter() - t0)
+            if wait > 0:
+                _time.sleep(wait)
+            D, n, link = bank[q % bank_size]
+            m, h = outs[q]
+            srv.submit(D, n, link, m, h)
+        submit_s = _time.perf_counter() - t0
+        rc = srv.drain()
+        st = srv.stats()
+    finally:
+        srv.close()
+    merges = sum(bank[q % bank_size][1] - 1 for q in range(n_requests))
+    return {
+        "metric": "served jobs/s and latency (Poisson 200 req/s, n log-uniform [256, 32768])",
+        "value": st["completed"] / st["wall_s"] if st["wall_s"] else None, "unit": "jobs/s",
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+        "requests": n_requests, "completed": st["completed"], "failed": st["failed"],
+        "offered_rate": n_requests / stream_specs[-1][0], "arrival_span_s": stream_specs[-1][0],
+        "submit_span_s": submit_s, "wall_s": st["wall_s"],
+        "merges_per_s": merges / st["wall_s"] if st["wall_s"] else None,
+        "peak_inflight": st["peak_inflight"], "peak_pool_bytes": st["peak_bytes"],
+        "pool_bytes": st["budget_bytes"], "lanes": 48, "status": rc,
+        "inputs": f"bank of {bank_size} matrices of the same request stream, generated on the device",
+    }
+
+
 def run_reference(args, world, rank, local):
     """The reference arm: the CPU oracle, each step a bounded sample."""
     if rank != 0:
@@ -467,6 +528,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload name (profiling uses smaller conformer<N> cases)")
     args = ap.parse_args(argv)

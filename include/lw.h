@@ -238,6 +238,61 @@ void lw_batch_destroy(lw_batch *batch);
 /* lw_cluster_batch -- create, run, wait and destroy in one blocking call. */
 lw_status lw_cluster_batch(lw_ctx *ctx, lw_job *jobs, int32_t njobs);
 
+/*
+ * Serving: a request loop with continuous batching.
+ *
+ * A server owns a device memory pool of `budget_bytes` and `lanes` execution
+ * lanes (a CUDA stream and a context each) on `device`.  Submitted requests
+ * queue on the host; a scheduler thread admits one as soon as a lane is free
+ * and the pool can hold its packed matrix (n(n-1)/2 * 4 bytes, rounded up to
+ * 256): the matrix is copied into the pool, clustered on the lane's stream,
+ * and the results copied to the caller's buffers.  Lanes run side by side,
+ * so requests that arrive while others are on the GPU start as soon as a
+ * lane and memory free up; a request that does not fit the pool yet is
+ * passed over by smaller ones behind it.  Every result is bit-identical to
+ * lw_cluster on the same input.  All server calls are thread-safe.
+ */
+typedef struct lw_server lw_server;
+
+typedef struct lw_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t peak_bytes;    /* largest sum of footprints admitted at once */
+    int64_t budget_bytes;  /* the pool size */
+    int32_t peak_inflight; /* most requests admitted at once */
+    int32_t pad;
+    double p50_ms, p99_ms, mean_ms; /* latency, submission to completion */
+    double wall_s;         /* first submission to last completion */
+} lw_server_stats;
+
+/* lw_server_create -- allocate the pool (one cudaMalloc of budget_bytes),
+ * the lanes (1..256) and start the scheduler.  LW_ERR_OOM if the pool does
+ * not fit, LW_ERR_INVALID_ARG for a bad device, budget or lane count. */
+lw_status lw_server_create(int device, int64_t budget_bytes, int32_t lanes, lw_server **out);
+
+/* lw_server_submit -- queue one request and return its ticket.  dist (host
+ * or device, read-only, pinned host memory for an asynchronous copy),
+ * merges_out and heights_out (host or device) must stay valid until the
+ * request completes.  LW_ERR_INVALID_ARG for bad arguments or a matrix
+ * larger than the whole pool. */
+lw_status lw_server_submit(lw_server *srv, const float *dist, int64_t n, int linkage,
+                           int32_t *merges_out, float *heights_out, uint64_t *ticket);
+
+/* lw_server_poll -- *done = 1 once the request finished; then *status is its
+ * lw_status and *latency_ms the time from submission to completion. */
+lw_status lw_server_poll(lw_server *srv, uint64_t ticket, int32_t *done, lw_status *status,
+                         double *latency_ms);
+
+/* lw_server_drain -- block until every submitted request finished; returns
+ * LW_OK if all succeeded. */
+lw_status lw_server_drain(lw_server *srv);
+
+/* lw_server_get_stats -- counters, latency percentiles and wall time. */
+lw_status lw_server_get_stats(lw_server *srv, lw_server_stats *stats);
+
+/* lw_server_destroy -- finish the queued work, stop the scheduler, free
+ * everything (NULL is a no-op). */
+void lw_server_destroy(lw_server *srv);
+
 /* lw_status_string -- static text for a status code. */
 const char *lw_status_string(lw_status s);
 

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "liblw.so")
-SOURCES = ["lw_merge.cu", "lw_api.cu", "lw_noalloc.cu"]
+SOURCES = ["lw_merge.cu", "lw_api.cu", "lw_noalloc.cu", "lw_server.cu"]
 HEADERS = ["lw_internal.h", os.path.join("..", "..", "include", "lw.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -28,8 +28,21 @@ STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW
 EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
            "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy",
            "lw_batch_create", "lw_batch_run", "lw_batch_wait", "lw_batch_destroy",
-           "lw_cluster_batch", "lw_cluster_noalloc")
+           "lw_cluster_batch", "lw_server_create", "lw_server_submit", "lw_server_poll",
+           "lw_server_drain", "lw_server_get_stats", "lw_server_destroy", "lw_cluster_noalloc")
 LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT = 4, 5
+
+
+class LwServerStats(ctypes.Structure):
+    """struct lw_server_stats of include/lw.h."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("peak_inflight", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
 
 
 class LwJob(ctypes.Structure):
@@ -92,6 +105,20 @@ def load(path: str = LIB_PATH):
         lib.lw_batch_destroy.restype = None
         lib.lw_cluster_batch.argtypes = [vp, jp, ctypes.c_int32]
         lib.lw_cluster_batch.restype = ctypes.c_int
+        lib.lw_server_create.argtypes = [ctypes.c_int, i64, ctypes.c_int32, ctypes.POINTER(vp)]
+        lib.lw_server_create.restype = ctypes.c_int
+        lib.lw_server_submit.argtypes = [vp, vp, i64, ctypes.c_int, vp, vp,
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        lib.lw_server_submit.restype = ctypes.c_int
+        lib.lw_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        lib.lw_server_poll.restype = ctypes.c_int
+        lib.lw_server_drain.argtypes = [vp]
+        lib.lw_server_drain.restype = ctypes.c_int
+        lib.lw_server_get_stats.argtypes = [vp, ctypes.POINTER(LwServerStats)]
+        lib.lw_server_get_stats.restype = ctypes.c_int
+        lib.lw_server_destroy.argtypes = [vp]
+        lib.lw_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -208,6 +235,59 @@ def lw_batch_destroy(batch: int) -> None:
 def lw_cluster_batch(ctx: int, jobs) -> int:
     """Blocking batch; fills jobs[q].status; returns the first failing status."""
     return int(load().lw_cluster_batch(ctx, jobs, len(jobs)))
+
+
+class Server:
+    """A continuous-batching request loop (lw_server_* of include/lw.h)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 1 << 30, lanes: int = 8):
+        lib = load()
+        h = ctypes.c_void_p()
+        s = lib.lw_server_create(int(device), int(budget_bytes), int(lanes), ctypes.byref(h))
+        if s != 0:
+            raise LwError(s, "lw_server_create")
+        self.handle = h.value
+
+    def submit(self, D, n: int, linkage, merges, heights) -> int:
+        if isinstance(linkage, str):
+            linkage = LINKAGES[linkage]
+        t = ctypes.c_uint64()
+        s = load().lw_server_submit(self.handle, _ptr(D) if n > 1 else None, int(n), int(linkage),
+                                    _ptr(merges) if n > 1 else None,
+                                    _ptr(heights) if n > 1 else None, ctypes.byref(t))
+        if s != 0:
+            raise LwError(s, "lw_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, status, latency_ms)."""
+        d = ctypes.c_int32()
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        s = load().lw_server_poll(self.handle, ticket, ctypes.byref(d), ctypes.byref(st),
+                                  ctypes.byref(lat))
+        if s != 0:
+            raise LwError(s, "lw_server_poll")
+        return bool(d.value), st.value, lat.value
+
+    def drain(self) -> int:
+        return int(load().lw_server_drain(self.handle))
+
+    def stats(self) -> dict:
+        st = LwServerStats()
+        load().lw_server_get_stats(self.handle, ctypes.byref(st))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            load().lw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lw_status_string(status: int) -> str:
