@@ -359,6 +359,8 @@ def run_batched(args, local, plain_sample: int = 256):
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream=stream)
     mats = [work[int(offs[q]):int(offs[q]) + sizes[q]] for q in range(len(specs))]
+    from paper_1709_06816_gb300 import autotune
+    classes = autotune.apply(ctx, local)
     table, outs = ctx.make_jobs(mats, [n for n, _, _ in specs], [l for _, l, _ in specs])
     plan = native.lw_batch_create(ctx.handle, table)
     total_merges = sum(n - 1 for n, _, _ in specs)
@@ -408,7 +410,8 @@ def run_batched(args, local, plain_sample: int = 256):
         "plain_jobs_per_s": plain_jobs_per_s, "plain_sample_jobs": len(pick),
         "speedup_vs_plain": jobs_per_s / plain_jobs_per_s,
         "step": "restore all matrices (one device copy) + one batch-plan run (CUDA graph: "
-                "queue reset + persistent CTA-per-job kernel)",
+                "per size class, queue reset + persistent CTA-per-job kernel, classes side by side)",
+        "classes": classes,
     }
 
 

@@ -148,7 +148,10 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..13]);
  *   LW_OPT_BATCH_SPLIT  largest n a batch runs on a single CTA (0: the
  *                     largest that fits one CTA's shared memory); larger
- *                     jobs of a batch run over the whole device.
+ *                     jobs of a batch run over the whole device;
+ *   LW_OPT_CTA_THREADS  threads per CTA of lw_cluster's kernel: 128, 256 or
+ *                     512 (0: 512).  Smaller CTAs suit small matrices run
+ *                     side by side (several fit one SM).
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
 enum {
@@ -156,7 +159,8 @@ enum {
     LW_OPT_TIMEOUT_MS = 2,
     LW_OPT_TEST_SKIP_ARRIVE = 3,
     LW_OPT_PHASE_TIMES = 4,
-    LW_OPT_BATCH_SPLIT = 5
+    LW_OPT_BATCH_SPLIT = 5,
+    LW_OPT_CTA_THREADS = 6
 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
@@ -234,6 +238,18 @@ lw_status lw_batch_wait(lw_batch *batch, lw_job *jobs);
 
 /* lw_batch_destroy -- free the plan (NULL is a no-op). */
 void lw_batch_destroy(lw_batch *batch);
+
+/*
+ * lw_set_batch_classes -- how one-CTA batch jobs are grouped: class q takes
+ * the jobs with n_hi[q-1] < n <= n_hi[q] (n_hi ascending, count <= 16) and
+ * runs them with CTAs of cta_threads[q] threads (128, 256 or 512: smaller
+ * CTAs let several jobs share an SM).  Each class is its own persistent
+ * launch; the classes run side by side as branches of the batch's CUDA
+ * graph.  count = 0 restores the default (one class of 512-thread CTAs).
+ * The autotuner of the Python package measures and sets this table.
+ */
+lw_status lw_set_batch_classes(lw_ctx *ctx, const int64_t *n_hi, const int32_t *cta_threads,
+                               int32_t count);
 
 /* lw_cluster_batch -- create, run, wait and destroy in one blocking call. */
 lw_status lw_cluster_batch(lw_ctx *ctx, lw_job *jobs, int32_t njobs);

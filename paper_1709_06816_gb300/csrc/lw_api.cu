@@ -21,10 +21,12 @@ struct lw_ctx {
     bool own_stream = false;
     int num_sms = 0;
     int grid_opt = 0;
+    int cta_threads = lw::kThreads;  // CTA size of the merge kernel (128, 256, 512)
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
     int phase_timing = 0;
     long long batch_split = 0;  // 0: largest n one CTA can hold
+    std::vector<std::pair<long long, int>> batch_classes;  // (n_hi, CTA threads)
 
     // device workspace
     void *ws = nullptr;
@@ -127,11 +129,12 @@ int choose_grid(lw_ctx *ctx, long long n)
     const long long nb = (n + lw::kRowBlock - 1) / lw::kRowBlock;
     if (G > nb)
         G = (int)nb;
-    while (G < ctx->num_sms && !lw::merge_config_ok(n, G, ctx->num_sms))
+    const int nt = ctx->cta_threads;
+    while (G < ctx->num_sms && !lw::merge_config_ok(n, G, ctx->num_sms, nt))
         ++G;  // too much shared memory per CTA: spread the rows wider
-    while (G > 1 && !lw::merge_config_ok(n, G, ctx->num_sms))
+    while (G > 1 && !lw::merge_config_ok(n, G, ctx->num_sms, nt))
         --G;
-    return lw::merge_config_ok(n, G, ctx->num_sms) ? G : 0;
+    return lw::merge_config_ok(n, G, ctx->num_sms, nt) ? G : 0;
 }
 
 // Queue one run on ctx->stream.  dist/merges/heights are device pointers.
@@ -174,7 +177,7 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     // barrier, status and stats words are contiguous
     if ((e = cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
-    if ((e = lw::launch_merge(p, ctx->stream)) != cudaSuccess)
+    if ((e = lw::launch_merge(p, ctx->cta_threads, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaLaunchCooperativeKernel");
     return LW_OK;
 }
@@ -414,6 +417,11 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
     case LW_OPT_PHASE_TIMES:
         ctx->phase_timing = value != 0;
         return LW_OK;
+    case LW_OPT_CTA_THREADS:
+        if (value != 0 && value != 128 && value != 256 && value != 512)
+            return LW_ERR_INVALID_ARG;
+        ctx->cta_threads = value == 0 ? lw::kThreads : (int)value;
+        return LW_OK;
     case LW_OPT_BATCH_SPLIT:
         if (value < 0)
             return LW_ERR_INVALID_ARG;
@@ -430,28 +438,38 @@ struct lw_batch {
     lw_ctx *ctx = nullptr;
     int njobs = 0;
     std::vector<lw_job> jobs;        // host copy of the table
-    std::vector<int> small_idx;      // jobs run one per CTA
     std::vector<int> big_idx;        // jobs run over the whole device
-    lw::BatchJob *d_jobs = nullptr;  // small-job table
-    int *d_status = nullptr;         // [small] statuses, then [big] statuses
-    int *d_queue = nullptr;
+    struct Class {
+        long long n_hi = 0;          // jobs with n <= n_hi (and above the previous class)
+        int nt = lw::kThreads;       // threads per CTA
+        std::vector<int> idx;        // job indices
+        long long n_max = 0;
+        int grid = 0;
+        lw::BatchJob *d_jobs = nullptr;
+        char *d_ws = nullptr;
+        int status_off = 0;
+        cudaStream_t side = nullptr;
+        cudaEvent_t join = nullptr;
+    };
+    std::vector<Class> classes;
+    int *d_status = nullptr;         // per class, then [big] statuses
+    int *d_queue = nullptr;          // one counter per class
     long long *d_merges = nullptr;
-    char *d_ws = nullptr;
-    int grid = 0;
-    long long n_max = 0;
+    cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
 
-// Largest n whose one-CTA shared memory fits (and lets at least one CTA run).
-long long batch_auto_split()
+// Largest n whose one-CTA shared memory fits (and lets at least one CTA of
+// nt threads run).
+long long batch_auto_split(int nt)
 {
     long long lo = 2, hi = 1 << 16;
     while (lo < hi) {
         const long long mid = (lo + hi + 1) / 2;
-        if (lw::batch_ctas_per_sm(mid) >= 1)
+        if (lw::batch_ctas_per_sm(mid, nt) >= 1)
             lo = mid;
         else
             hi = mid - 1;
@@ -467,11 +485,19 @@ void batch_free(lw_batch *b)
         cudaGraphExecDestroy(b->exec);
     if (b->graph)
         cudaGraphDestroy(b->graph);
-    cudaFree(b->d_jobs);
+    for (auto &c : b->classes) {
+        cudaFree(c.d_jobs);
+        cudaFree(c.d_ws);
+        if (c.side)
+            cudaStreamDestroy(c.side);
+        if (c.join)
+            cudaEventDestroy(c.join);
+    }
+    if (b->fork)
+        cudaEventDestroy(b->fork);
     cudaFree(b->d_status);
     cudaFree(b->d_queue);
     cudaFree(b->d_merges);
-    cudaFree(b->d_ws);
     cudaGetLastError();
     delete b;
 }
@@ -479,6 +505,23 @@ void batch_free(lw_batch *b)
 }  // namespace
 
 extern "C" {
+
+lw_status lw_set_batch_classes(lw_ctx *ctx, const int64_t *n_hi, const int32_t *cta_threads,
+                               int32_t count)
+{
+    if (!ctx || count < 0 || count > 16 || (count > 0 && (!n_hi || !cta_threads)))
+        return LW_ERR_INVALID_ARG;
+    std::vector<std::pair<long long, int>> cl;
+    for (int q = 0; q < count; ++q) {
+        const int nt = cta_threads[q];
+        if ((nt != 128 && nt != 256 && nt != 512) || n_hi[q] < 2 ||
+            (q > 0 && n_hi[q] <= n_hi[q - 1]))
+            return LW_ERR_INVALID_ARG;
+        cl.emplace_back((long long)n_hi[q], nt);
+    }
+    ctx->batch_classes = cl;
+    return LW_OK;
+}
 
 lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_batch **out)
 {
@@ -499,7 +542,19 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
     b->ctx = ctx;
     b->njobs = njobs;
     b->jobs.assign(jobs, jobs + njobs);
-    const long long split = ctx->batch_split > 0 ? ctx->batch_split : batch_auto_split();
+    // classes of one-CTA jobs: the tuned table, or one class of 512-thread
+    // CTAs up to the largest n one CTA can hold; then the split option caps it
+    std::vector<std::pair<long long, int>> cl = ctx->batch_classes;
+    if (cl.empty())
+        cl.emplace_back(batch_auto_split(lw::kThreads), lw::kThreads);
+    const long long cap = ctx->batch_split > 0 ? ctx->batch_split : cl.back().first;
+    for (auto &c : cl) {
+        lw_batch::Class k;
+        k.n_hi = c.first < cap ? c.first : cap;
+        k.nt = c.second;
+        if (b->classes.empty() || k.n_hi > b->classes.back().n_hi)
+            b->classes.push_back(k);
+    }
     long long big_n = 0;
     for (int q = 0; q < njobs; ++q) {
         const lw_job &J = jobs[q];
@@ -510,15 +565,20 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
             batch_free(b);
             return LW_ERR_INVALID_ARG;
         }
-        if (J.n <= split) {
-            b->small_idx.push_back(q);
-            b->n_max = J.n > b->n_max ? J.n : b->n_max;
-        } else {
+        bool placed = false;
+        for (auto &c : b->classes) {
+            if (J.n <= c.n_hi) {
+                c.idx.push_back(q);
+                c.n_max = J.n > c.n_max ? J.n : c.n_max;
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) {
             b->big_idx.push_back(q);
             big_n = J.n > big_n ? J.n : big_n;
         }
     }
-    const size_t nsmall = b->small_idx.size(), nbig = b->big_idx.size();
     lw_status st = LW_OK;
     auto alloc = [&](void **pp, size_t bytes, const char *what) {
         if (st != LW_OK)
@@ -530,13 +590,22 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
             st = LW_ERR_OOM;
         }
     };
-    alloc((void **)&b->d_status, sizeof(int) * (nsmall + nbig), "batch statuses");
-    alloc((void **)&b->d_queue, sizeof(int), "batch queue");
+    int nstat = (int)b->big_idx.size();
+    for (auto &c : b->classes) {
+        c.status_off = nstat;
+        nstat += (int)c.idx.size();
+    }
+    alloc((void **)&b->d_status, sizeof(int) * (size_t)(nstat > 0 ? nstat : 1), "batch statuses");
+    alloc((void **)&b->d_queue, sizeof(int) * b->classes.size(), "batch queues");
     alloc((void **)&b->d_merges, sizeof(long long), "batch counter");
-    if (nsmall > 0) {
-        std::vector<lw::BatchJob> table(nsmall);
-        for (size_t q = 0; q < nsmall; ++q) {
-            const lw_job &J = jobs[b->small_idx[q]];
+    bool any_small = false;
+    for (auto &c : b->classes) {
+        if (c.idx.empty() || st != LW_OK)
+            continue;
+        any_small = true;
+        std::vector<lw::BatchJob> table(c.idx.size());
+        for (size_t q = 0; q < c.idx.size(); ++q) {
+            const lw_job &J = jobs[c.idx[q]];
             table[q].D = J.dist;
             table[q].n = J.n;
             table[q].linkage = J.linkage;
@@ -544,48 +613,69 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
             table[q].merges = J.merges_out;
             table[q].heights = J.heights_out;
         }
-        const int per_sm = lw::batch_ctas_per_sm(b->n_max < 2 ? 2 : b->n_max);
-        if (per_sm < 1 && st == LW_OK) {
-            set_err(ctx, "batch jobs of n=%lld do not fit one CTA", b->n_max);
+        const int per_sm = lw::batch_ctas_per_sm(c.n_max < 2 ? 2 : c.n_max, c.nt);
+        if (per_sm < 1) {
+            set_err(ctx, "batch jobs of n=%lld do not fit one CTA of %d threads", c.n_max, c.nt);
             st = LW_ERR_INVALID_ARG;
+            break;
         }
-        b->grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
-        if ((size_t)b->grid > nsmall)
-            b->grid = (int)nsmall;
-        const lw::WorkspaceLayout L = lw::workspace_layout(b->n_max, 1);
-        alloc((void **)&b->d_jobs, sizeof(lw::BatchJob) * nsmall, "batch table");
-        alloc((void **)&b->d_ws, L.total * (size_t)b->grid, "batch slots");
+        c.grid = ctx->num_sms * per_sm;
+        if ((size_t)c.grid > c.idx.size())
+            c.grid = (int)c.idx.size();
+        const lw::WorkspaceLayout L = lw::workspace_layout(c.n_max, 1);
+        alloc((void **)&c.d_jobs, sizeof(lw::BatchJob) * c.idx.size(), "batch table");
+        alloc((void **)&c.d_ws, L.total * (size_t)c.grid, "batch slots");
         if (st == LW_OK &&
-            (e = cudaMemcpy(b->d_jobs, table.data(), sizeof(lw::BatchJob) * nsmall,
+            (e = cudaMemcpy(c.d_jobs, table.data(), sizeof(lw::BatchJob) * c.idx.size(),
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             st = cuda_fail(ctx, e, "cudaMemcpy(batch table)");
-        // record the small-job launch as a graph: reset the queue, run the batch kernel
-        if (st == LW_OK) {
-            lw::BatchParams bp;
-            bp.jobs = b->d_jobs;
-            bp.njobs = (int)nsmall;
-            bp.n_max = b->n_max;
-            bp.queue = b->d_queue;
-            bp.ws = b->d_ws;
-            bp.job_status = b->d_status;
-            bp.merges_done = b->d_merges;
-            bp.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
-            e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                cudaMemsetAsync(b->d_queue, 0, sizeof(int), ctx->stream);
-                cudaMemsetAsync(b->d_merges, 0, sizeof(long long), ctx->stream);
-                cudaError_t el = lw::launch_batch(bp, b->grid, ctx->stream);
-                e = cudaStreamEndCapture(ctx->stream, &b->graph);
-                if (e == cudaSuccess)
-                    e = el;
-            }
-            if (e == cudaSuccess)
-                e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-            if (e != cudaSuccess)
-                st = cuda_fail(ctx, e, "batch graph capture");
-        }
+        if (st == LW_OK && (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming) != cudaSuccess))
+            st = cuda_fail(ctx, cudaGetLastError(), "batch streams");
     }
-    if (st == LW_OK && nbig > 0) {
+    // record the one-CTA launches as one graph: every class on its own branch
+    // (reset its queue, run its persistent kernel), all branches joined
+    if (st == LW_OK && any_small) {
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+            st = cuda_fail(ctx, cudaGetLastError(), "batch event");
+    }
+    if (st == LW_OK && any_small) {
+        e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t el = cudaSuccess;
+        if (e == cudaSuccess) {
+            cudaEventRecord(b->fork, ctx->stream);
+            cudaMemsetAsync(b->d_merges, 0, sizeof(long long), ctx->stream);
+            for (size_t k = 0; k < b->classes.size(); ++k) {
+                auto &c = b->classes[k];
+                if (c.idx.empty())
+                    continue;
+                cudaStreamWaitEvent(c.side, b->fork, 0);
+                cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), c.side);
+                lw::BatchParams bp;
+                bp.jobs = c.d_jobs;
+                bp.njobs = (int)c.idx.size();
+                bp.n_max = c.n_max;
+                bp.queue = b->d_queue + k;
+                bp.ws = c.d_ws;
+                bp.job_status = b->d_status + c.status_off;
+                bp.merges_done = b->d_merges;
+                bp.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
+                cudaError_t e2 = lw::launch_batch(bp, c.grid, c.nt, c.side);
+                if (el == cudaSuccess)
+                    el = e2;
+                cudaEventRecord(c.join, c.side);
+                cudaStreamWaitEvent(ctx->stream, c.join, 0);
+            }
+            e = cudaStreamEndCapture(ctx->stream, &b->graph);
+            if (e == cudaSuccess)
+                e = el;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess)
+            st = cuda_fail(ctx, e, "batch graph capture");
+    }
+    if (st == LW_OK && !b->big_idx.empty()) {
         // size the context's workspace now so that runs never allocate
         const int G = choose_grid(ctx, big_n);
         if (G <= 0) {
@@ -619,13 +709,12 @@ lw_status lw_batch_run(lw_batch *b)
         return cuda_fail(ctx, e, "cudaSetDevice");
     if (b->exec && (e = cudaGraphLaunch(b->exec, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaGraphLaunch");
-    const size_t nsmall = b->small_idx.size();
     for (size_t q = 0; q < b->big_idx.size(); ++q) {
         const lw_job &J = b->jobs[b->big_idx[q]];
         lw_status s = enqueue(ctx, J.dist, J.n, J.linkage, J.merges_out, J.heights_out);
         if (s != LW_OK)
             return s;
-        if ((e = cudaMemcpyAsync(b->d_status + nsmall + q, ctx->d_status, sizeof(int),
+        if ((e = cudaMemcpyAsync(b->d_status + q, ctx->d_status, sizeof(int),
                                  cudaMemcpyDeviceToDevice, ctx->stream)) != cudaSuccess)
             return cuda_fail(ctx, e, "cudaMemcpyAsync(job status)");
     }
@@ -640,15 +729,16 @@ lw_status lw_batch_wait(lw_batch *b, lw_job *jobs)
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "cudaStreamSynchronize");
-    const size_t nsmall = b->small_idx.size(), nbig = b->big_idx.size();
-    std::vector<int> st(nsmall + nbig, 0);
+    std::vector<int> idx = b->big_idx;
+    for (auto &c : b->classes)
+        idx.insert(idx.end(), c.idx.begin(), c.idx.end());
+    std::vector<int> st(idx.size(), 0);
     if (!st.empty() &&
         (e = cudaMemcpy(st.data(), b->d_status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost)) !=
             cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemcpy(job statuses)");
     lw_status first = LW_OK;
     for (size_t q = 0; q < st.size(); ++q) {
-        const int idx = q < nsmall ? b->small_idx[q] : b->big_idx[q - nsmall];
         lw_status js = LW_OK;
         switch (st[q]) {
         case 0: js = LW_OK; break;
@@ -657,10 +747,10 @@ lw_status lw_batch_wait(lw_batch *b, lw_job *jobs)
         default: js = LW_ERR_CUDA; break;
         }
         if (jobs)
-            jobs[idx].status = js;
+            jobs[idx[q]].status = js;
         if (js != LW_OK && first == LW_OK) {
             first = js;
-            set_err(ctx, "job %d: %s", idx, lw_status_string(js));
+            set_err(ctx, "job %d: %s", idx[q], lw_status_string(js));
         }
     }
     return first;

@@ -7,8 +7,7 @@
 
 namespace lw {
 
-constexpr int kThreads = 512;            // threads per CTA of the merge kernel
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = 512;            // default threads per CTA of the merge kernel
 constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
 constexpr int kCacheKeys = 4;            // smallest keys cached per row
 constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
@@ -99,14 +98,18 @@ struct BatchParams {
 
 // Bytes of dynamic shared memory the merge kernel needs for (n, G).
 size_t merge_smem_bytes(long long n, int G);
-// True if a grid of G CTAs for n objects fits co-resident on the current device.
-bool merge_config_ok(long long n, int G, int num_sms);
-// Launch the persistent kernel cooperatively on `stream`.
-cudaError_t launch_merge(const MergeParams &p, cudaStream_t stream);
-// CTAs of the batch kernel that fit on one SM for jobs up to n_max.
-int batch_ctas_per_sm(long long n_max);
-// Launch the batch kernel (grid CTAs, one workspace slot each) on `stream`;
-// call batch_ctas_per_sm(bp.n_max) first (it sets the shared-memory limit).
-cudaError_t launch_batch(const BatchParams &bp, int grid, cudaStream_t stream);
+// CTA sizes the kernels are built for: 128, 256 or 512 threads (4, 2 or 1
+// CTAs per SM by registers).
+// True if a grid of G CTAs of nt threads for n objects fits co-resident on
+// the current device.
+bool merge_config_ok(long long n, int G, int num_sms, int nt = kThreads);
+// Launch the persistent kernel (CTAs of nt threads) cooperatively on `stream`.
+cudaError_t launch_merge(const MergeParams &p, int nt, cudaStream_t stream);
+// CTAs of nt threads of the batch kernel that fit on one SM for jobs up to n_max.
+int batch_ctas_per_sm(long long n_max, int nt = kThreads);
+// Launch the batch kernel (grid CTAs of nt threads, one workspace slot each) on
+// `stream`; call batch_ctas_per_sm(bp.n_max, nt) first (it sets the
+// shared-memory limit).
+cudaError_t launch_batch(const BatchParams &bp, int grid, int nt, cudaStream_t stream);
 
 }  // namespace lw

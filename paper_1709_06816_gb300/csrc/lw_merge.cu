@@ -197,11 +197,12 @@ __device__ __forceinline__ Cand warp_cand_min(Cand v)
     return out;
 }
 
+template <int NT>
 struct Shared {
-    Cand red[kWarps + 1];
-    u64 tk[kWarps][K];
+    Cand red[(NT / 32) + 1];
+    u64 tk[(NT / 32)][K];
     u64 tko[K];
-    int wcnt[kWarps];        // per-warp request counts (prefix sums)
+    int wcnt[(NT / 32)];        // per-warp request counts (prefix sums)
     int flag;
     int nresc;               // rows to rescan at once this merge
     int nexec;               // refill rows served this merge
@@ -218,7 +219,8 @@ struct Shared {
 // (deterministic, the same in every CTA), cut at kMaxReq.  Thread t holds
 // CTA t's record (cnt requests in rq).  Sets sh.exec_row, sh.nexec and
 // sh.my_off (the position of this CTA's first request).
-__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], int b, Shared &sh)
+template <int NT>
+__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = cnt;
@@ -247,23 +249,24 @@ __device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], in
         sh.my_off = off0;
     if (warp == 0) {
         Cand w = {kNoKey, 0xffffffffu};
-        if (lane < kWarps)
+        if (lane < (NT / 32))
             w = sh.red[lane];
         w = warp_cand_min(w);
-        int tot = lane < kWarps ? sh.wcnt[lane] : 0;
+        int tot = lane < (NT / 32) ? sh.wcnt[lane] : 0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
             tot += __shfl_xor_sync(0xffffffffu, tot, off);
         if (lane == 0) {
-            sh.red[kWarps] = w;
+            sh.red[(NT / 32)] = w;
             sh.nexec = tot < kMaxReq ? tot : kMaxReq;
         }
     }
     __syncthreads();
-    return sh.red[kWarps];
+    return sh.red[(NT / 32)];
 }
 
-__device__ Cand block_cand_min(Cand v, Shared &sh)
+template <int NT>
+__device__ Cand block_cand_min(Cand v, Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_cand_min(v);
@@ -272,18 +275,19 @@ __device__ Cand block_cand_min(Cand v, Shared &sh)
     __syncthreads();
     if (warp == 0) {
         Cand w = {kNoKey, 0xffffffffu};
-        if (lane < kWarps)
+        if (lane < (NT / 32))
             w = sh.red[lane];
         w = warp_cand_min(w);
         if (lane == 0)
-            sh.red[kWarps] = w;
+            sh.red[(NT / 32)] = w;
     }
     __syncthreads();
-    return sh.red[kWarps];
+    return sh.red[(NT / 32)];
 }
 
 // K smallest keys over every thread's list; result in sh.tko (all threads).
-__device__ void block_topk(u64 (&L)[K], Shared &sh)
+template <int NT>
+__device__ void block_topk(u64 (&L)[K], Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u64 w[K];
@@ -298,7 +302,7 @@ __device__ void block_topk(u64 (&L)[K], Shared &sh)
         u64 M[K];
 #pragma unroll
         for (int q = 0; q < K; ++q)
-            M[q] = lane < kWarps ? sh.tk[lane][q] : kNoKey;
+            M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
         warp_topk(M, w);
         if (lane == 0) {
 #pragma unroll
@@ -310,8 +314,9 @@ __device__ void block_topk(u64 (&L)[K], Shared &sh)
 }
 
 // Both reductions a CTA publishes, in one pass: the candidate minimum (in
-// sh.red[kWarps]) and the K smallest survivor-row keys (in sh.tko).
-__device__ void block_publish(Cand c, u64 (&L)[K], Shared &sh)
+// sh.red[(NT / 32)]) and the K smallest survivor-row keys (in sh.tko).
+template <int NT>
+__device__ void block_publish(Cand c, u64 (&L)[K], Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u64 w[K];
@@ -329,13 +334,13 @@ __device__ void block_publish(Cand c, u64 (&L)[K], Shared &sh)
         u64 M[K];
 #pragma unroll
         for (int q = 0; q < K; ++q)
-            M[q] = lane < kWarps ? sh.tk[lane][q] : kNoKey;
-        if (lane < kWarps)
+            M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
+        if (lane < (NT / 32))
             x = sh.red[lane];
         warp_topk(M, w);
         x = warp_cand_min(x);
         if (lane == 0) {
-            sh.red[kWarps] = x;
+            sh.red[(NT / 32)] = x;
 #pragma unroll
             for (int q = 0; q < K; ++q)
                 sh.tko[q] = w[q];
@@ -360,7 +365,8 @@ __device__ __forceinline__ void grid_arrive(const MergeParams &p, unsigned &epoc
     }
 }
 
-__device__ bool grid_wait(const MergeParams &p, unsigned epoch, Shared &sh)
+template <int NT>
+__device__ bool grid_wait(const MergeParams &p, unsigned epoch, Shared<NT> &sh)
 {
     if (threadIdx.x == 0) {
         int st = 0;
@@ -467,7 +473,8 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
 // K smallest keys of row r over live columns, computed by the whole CTA
 // (for a row whose cache empties before its refill arrives).  Adds the live
 // cells read to `live_cells`.  Result in sh.tko.
-__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared &sh,
+template <int NT>
+__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT> &sh,
                                long long &live_cells)
 {
     const long long n = p.n;
@@ -479,7 +486,7 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
     for (int q = 0; q < K; ++q)
         L[q] = kNoKey;
     long long cnt = 0;
-    for (long long q = start + threadIdx.x; q < end; q += kThreads) {
+    for (long long q = start + threadIdx.x; q < end; q += NT) {
         const long long c = q + base_c;
         if (live(bitmap, c)) {
             list_insert(L, make_key(__ldcg(p.D + q), (unsigned)c));
@@ -510,7 +517,8 @@ __device__ __forceinline__ void publish_list(u64 *dst, const u64 *src, int tid)
 // All n - 1 merges of one job, run by CTA b of the job's G CTAs (every CTA
 // of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
 // bytes of dynamic shared memory.
-__device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared &sh)
+template <int NT>
+__device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared<NT> &sh)
 {
     const long long n = p.n;
     const int G = p.G;
@@ -567,17 +575,17 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     };
 
     // ---- setup
-    for (long long w = tid; w < nwords; w += kThreads) {
+    for (long long w = tid; w < nwords; w += NT) {
         const long long live_n = n - w * 32;
         bitmap[w] = live_n >= 32 ? 0xffffffffu : ((1u << live_n) - 1u);
     }
-    for (int l = tid; l < R; l += kThreads) {
+    for (int l = tid; l < R; l += NT) {
         rsize[l] = 1;
         pend_t[l] = -1;
         upd[l] = kNoKey;
         upd[Rmax + l] = kNoKey;
     }
-    for (long long r = (long long)b * kThreads + tid; r < n; r += (long long)G * kThreads)
+    for (long long r = (long long)b * NT + tid; r < n; r += (long long)G * NT)
         p.size_g[r] = 1;
     if (tid == 0) {
         sh.nresc = 0;
@@ -592,7 +600,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     // triangle, so every CTA reads about the same number of cells)
     {
         int bad = 0;
-        for (int l = warp; l < R; l += kWarps) {
+        for (int l = warp; l < R; l += (NT / 32)) {
             const long long r = row_of(l);
             u64 top[K];
 #pragma unroll
@@ -618,7 +626,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     // first records: each CTA's smallest cached key, no refill requests
     {
         Cand c = {kNoKey, 0xffffffffu};
-        for (int l = tid; l < R; l += kThreads) {
+        for (int l = tid; l < R; l += NT) {
             if (ccnt[l] > 0) {
                 const u64 k = ck[l];
                 Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
@@ -824,7 +832,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         for (int q = 0; q < K; ++q)
             il[q] = kNoKey;
         u64 *updt = upd + (size_t)par * Rmax;
-        for (int l = tid; l < R; l += kThreads) {
+        for (int l = tid; l < R; l += NT) {
             const long long k = row_of(l);
             if (k >= n || k == i || k == j || !live(bitmap, k))
                 continue;
@@ -929,7 +937,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         // part of the survivor row
         {
             Cand c = {kNoKey, 0xffffffffu};
-            for (int l = tid; l < R; l += kThreads) {
+            for (int l = tid; l < R; l += NT) {
                 if (ccnt[l] > 0) {
                     const u64 k = ck[l];
                     Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
@@ -945,7 +953,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
             block_publish(c, il, sh);
             if (tid == 0) {
-                Cand x = sh.red[kWarps];
+                Cand x = sh.red[(NT / 32)];
                 const u64 h0 = sh.tko[0];
                 if (h0 != kNoKey) {
                     const Cand o = {(h0 & 0xffffffff00000000ull) | (u64)i, (unsigned)h0};
@@ -982,7 +990,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         {
             const int nexec = sh.nexec;
             const int sbuf = (int)(t % 3);
-            for (int s = warp; s < nexec; s += kWarps) {
+            for (int s = warp; s < nexec; s += (NT / 32)) {
                 const long long r = sh.exec_row[s];
                 if (r < 0 || r >= n || r == i || r == j)
                     continue;  // the owner drops this refill
@@ -1052,21 +1060,23 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) merge_kernel(MergeParams p)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) merge_kernel(MergeParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
-    merge_job(p, blockIdx.x, smem_raw, sh);
+    __shared__ Shared<NT> sh;
+    merge_job<NT>(p, blockIdx.x, smem_raw, sh);
 }
 
 // Many independent jobs in one persistent launch: each CTA takes the next job
 // from a queue (atomicAdd on a counter) and runs all its merges alone (a
 // one-CTA job needs no grid barrier), then takes another, until the queue is
 // empty.  CTA c keeps its scratch in workspace slot c.
-__global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
+    __shared__ Shared<NT> sh;
     __shared__ int job;
     const WorkspaceLayout L = workspace_layout(bp.n_max, 1);
     char *ws = bp.ws + (size_t)blockIdx.x * L.total;
@@ -1098,11 +1108,11 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp)
         p.skip_arrive_cta = -1;
         p.timing = 0;
         // the slot keeps the previous job's words: clear the ones that must start at zero
-        for (size_t q = threadIdx.x; q < (L.total - L.zero) / 4; q += kThreads)
+        for (size_t q = threadIdx.x; q < (L.total - L.zero) / 4; q += NT)
             reinterpret_cast<int *>(ws + L.zero)[q] = 0;
         __syncthreads();
         if (J.n > 1)
-            merge_job(p, 0, smem_raw, sh);
+            merge_job<NT>(p, 0, smem_raw, sh);
         __syncthreads();
         if (threadIdx.x == 0) {
             bp.job_status[jb] = J.n > 1 ? __ldcg(p.status) : 0;
@@ -1123,62 +1133,88 @@ size_t merge_smem_bytes(long long n, int G)
     return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * (8 * K + 8 + 16 + 4 * 5));
 }
 
-bool merge_config_ok(long long n, int G, int num_sms)
+namespace {
+
+// The kernel instantiations: CTA size nt and the CTAs per SM its registers allow.
+const void *merge_fn(int nt)
 {
-    // threads [kThreads-1-kMaxReq, kThreads) read the refill requests, the
-    // first G threads the candidates: the two sets must not overlap
-    if (G < 1 || G > num_sms || G > kThreads - 1 - kMaxReq)
-        return false;
+    switch (nt) {
+    case 128: return (const void *)merge_kernel<128, 4>;
+    case 256: return (const void *)merge_kernel<256, 2>;
+    default: return (const void *)merge_kernel<512, 1>;
+    }
+}
+
+const void *batch_fn(int nt)
+{
+    switch (nt) {
+    case 128: return (const void *)batch_kernel<128, 4>;
+    case 256: return (const void *)batch_kernel<256, 2>;
+    default: return (const void *)batch_kernel<512, 1>;
+    }
+}
+
+size_t static_smem(int nt)
+{
+    switch (nt) {
+    case 128: return sizeof(Shared<128>);
+    case 256: return sizeof(Shared<256>);
+    default: return sizeof(Shared<512>);
+    }
+}
+
+int fit_per_sm(const void *fn, int nt, size_t smem)
+{
     int dev = 0, limit = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return false;
-    const size_t smem = merge_smem_bytes(n, G);
-    if (smem + sizeof(Shared) > (size_t)limit)
-        return false;
-    if (cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return false;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, merge_kernel, kThreads, smem) !=
-        cudaSuccess)
-        return false;
-    return per_sm >= 1;
-}
-
-int batch_ctas_per_sm(long long n_max)
-{
-    const size_t smem = merge_smem_bytes(n_max, 1);
-    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        return 0;
+    if (smem + static_smem(nt) > (size_t)limit)
+        return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess)
         return 0;
     return per_sm;
 }
 
-cudaError_t launch_batch(const BatchParams &bp, int grid, cudaStream_t stream)
+}  // namespace
+
+bool merge_config_ok(long long n, int G, int num_sms, int nt)
 {
-    // batch_ctas_per_sm(bp.n_max) has set the kernel's shared-memory limit
-    // (this launch may be recorded into a graph, where no attribute is set)
-    const size_t smem = merge_smem_bytes(bp.n_max, 1);
-    batch_kernel<<<grid, kThreads, smem, stream>>>(bp);
-    return cudaGetLastError();
+    // the first G threads read the CTAs' records
+    if (G < 1 || G > num_sms || G > nt)
+        return false;
+    return fit_per_sm(merge_fn(nt), nt, merge_smem_bytes(n, G)) >= 1;
 }
 
-cudaError_t launch_merge(const MergeParams &p, cudaStream_t stream)
+int batch_ctas_per_sm(long long n_max, int nt)
+{
+    return fit_per_sm(batch_fn(nt), nt, merge_smem_bytes(n_max, 1));
+}
+
+cudaError_t launch_batch(const BatchParams &bp, int grid, int nt, cudaStream_t stream)
+{
+    // batch_ctas_per_sm(bp.n_max, nt) has set the kernel's shared-memory limit
+    // (this launch may be recorded into a graph, where no attribute is set)
+    const size_t smem = merge_smem_bytes(bp.n_max, 1);
+    BatchParams q = bp;
+    void *args[] = {&q};
+    return cudaLaunchKernel(batch_fn(nt), dim3(grid), dim3(nt), args, smem, stream);
+}
+
+cudaError_t launch_merge(const MergeParams &p, int nt, cudaStream_t stream)
 {
     const size_t smem = merge_smem_bytes(p.n, p.G);
-    cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const void *fn = merge_fn(nt);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     MergeParams q = p;
     void *args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void *)merge_kernel, dim3(p.G), dim3(kThreads), args,
-                                       smem, stream);
+    return cudaLaunchCooperativeKernel(fn, dim3(p.G), dim3(nt), args, smem, stream);
 }
 
 }  // namespace lw

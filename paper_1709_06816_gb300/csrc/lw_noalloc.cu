@@ -122,7 +122,7 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
     // the scratch keeps the previous call's contents: the barrier,
     // status and stats words must start at zero
     if (cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, stream) != cudaSuccess ||
-        lw::launch_merge(p, stream) != cudaSuccess) {
+        lw::launch_merge(p, lw::kThreads, stream) != cudaSuccess) {
         cudaGetLastError();
         return LW_ERR_CUDA;
     }

@@ -9,9 +9,10 @@
 // while others are on the GPU start as soon as a lane and memory free up and
 // their work overlaps on the device.  A request that does not fit the pool at
 // the moment is passed over by smaller ones behind it (backfill); one that
-// can never fit is refused at submission.  The grids of the admitted requests
-// never add up to more CTAs than the device holds at once (one CTA of the
-// merge kernel per SM), so every cooperative grid is resident as a whole.
+// can never fit is refused at submission.  The multi-CTA grids of the admitted
+// requests never add up to more CTAs than the device holds at once (one
+// 512-thread CTA per SM), so no two cooperative grids can each hold part of
+// the device while waiting for the rest.
 //
 // Large requests run with a modest grid (one CTA per 1024 objects): a merge
 // of the persistent kernel is bound by barrier and memory latency far more
@@ -143,6 +144,9 @@ struct lw_server {
         }
     }
 
+    // One CTA for up to 2048 objects (of 128 or 256 threads, so that several
+    // small requests share an SM -- the batch autotuner's finding on GB300);
+    // above that, 512-thread CTAs, one per 1024 objects.
     int grid_for(int64_t n) const
     {
         if (n <= 2048)
@@ -150,6 +154,8 @@ struct lw_server {
         int G = (int)((n + 1023) / 1024);
         return std::min(G, num_sms);
     }
+
+    static int threads_for(int64_t n) { return n <= 1024 ? 128 : n <= 2048 ? 256 : 512; }
 
     // Launch request r on lane L (scheduler thread, mutex held).
     lw_status launch(Lane &L, const Request &r, size_t off)
@@ -180,6 +186,7 @@ struct lw_server {
             dh = L.dh;
         }
         lw_set_option(L.ctx, LW_OPT_GRID, grid_for(r.n));
+        lw_set_option(L.ctx, LW_OPT_CTA_THREADS, threads_for(r.n));
         lw_status s = lw_cluster_async(L.ctx, d, r.n, r.linkage, dm, dh);
         if (s != LW_OK)
             return s;
@@ -247,7 +254,8 @@ struct lw_server {
                     break;
                 // every admitted grid must fit the device at once: cooperative
                 // grids wait on each other only through their own barriers
-                const int ctas = it->n > 1 ? grid_for(it->n) : 0;
+                const int g = it->n > 1 ? grid_for(it->n) : 0;
+                const int ctas = g > 1 ? g : 0;  // one-CTA grids need no co-residency
                 if (ctas_inflight + ctas > num_sms) {
                     ++it;
                     continue;

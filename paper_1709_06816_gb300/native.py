@@ -28,9 +28,10 @@ STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW
 EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
            "lw_set_option", "lw_status_string", "lw_last_error", "lw_destroy",
            "lw_batch_create", "lw_batch_run", "lw_batch_wait", "lw_batch_destroy",
+           "lw_set_batch_classes",
            "lw_cluster_batch", "lw_server_create", "lw_server_submit", "lw_server_poll",
            "lw_server_drain", "lw_server_get_stats", "lw_server_destroy", "lw_cluster_noalloc")
-LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT = 4, 5
+LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT, LW_OPT_CTA_THREADS = 4, 5, 6
 
 
 class LwServerStats(ctypes.Structure):
@@ -103,6 +104,9 @@ def load(path: str = LIB_PATH):
         lib.lw_batch_wait.restype = ctypes.c_int
         lib.lw_batch_destroy.argtypes = [vp]
         lib.lw_batch_destroy.restype = None
+        lib.lw_set_batch_classes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_int32]
+        lib.lw_set_batch_classes.restype = ctypes.c_int
         lib.lw_cluster_batch.argtypes = [vp, jp, ctypes.c_int32]
         lib.lw_cluster_batch.restype = ctypes.c_int
         lib.lw_server_create.argtypes = [ctypes.c_int, i64, ctypes.c_int32, ctypes.POINTER(vp)]
@@ -334,6 +338,18 @@ class Context:
 
     def set_phase_timing(self, on: bool = True):
         lw_set_option(self.handle, 4, 1 if on else 0)
+
+    def set_batch_classes(self, classes):
+        """classes: [(n_hi, cta_threads), ...] ascending in n_hi; [] = default."""
+        k = len(classes)
+        nh = (ctypes.c_int64 * max(k, 1))(*[int(a) for a, _ in classes])
+        nt = (ctypes.c_int32 * max(k, 1))(*[int(b) for _, b in classes])
+        s = load().lw_set_batch_classes(self.handle, nh, nt, k)
+        if s != 0:
+            raise LwError(s, f"lw_set_batch_classes({classes})")
+
+    def set_cta_threads(self, nt: int):
+        lw_set_option(self.handle, LW_OPT_CTA_THREADS, nt)
 
     def set_batch_split(self, n: int):
         lw_set_option(self.handle, LW_OPT_BATCH_SPLIT, n)

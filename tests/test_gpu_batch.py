@@ -134,3 +134,17 @@ def test_batch_many_copies_of_a_rescan_heavy_job(ctx):
             assert s == 0
             assert np.array_equal(m.cpu().numpy(), wm)
             assert np.array_equal(_bits(h.cpu().numpy()), _bits(wh))
+
+
+def test_batch_size_classes(ctx):
+    """Jobs split over three classes of CTA sizes (128, 256, 512 threads), each
+    its own persistent launch on a branch of the graph, plus grid-path jobs."""
+    ctx.set_batch_classes([(300, 128), (900, 256), (1600, 512)])
+    jobs = _mixed_jobs(60, 6, n_lo=2, n_hi=2200)
+    mats = [torch.from_numpy(D).cuda() for D, _, _ in jobs]
+    outs, st = ctx.cluster_batch(mats, [n for _, n, _ in jobs], [l for _, _, l in jobs])
+    _check(outs, st, jobs)
+    with pytest.raises(LwError):
+        ctx.set_batch_classes([(900, 256), (300, 128)])  # not ascending
+    with pytest.raises(LwError):
+        ctx.set_batch_classes([(900, 200)])  # not a built CTA size

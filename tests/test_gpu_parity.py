@@ -73,6 +73,24 @@ def test_small_multi_cta(ctx, link, grid):
                          f"n={n} grid={grid}")
 
 
+@pytest.mark.parametrize("nt", [128, 256])
+def test_smaller_ctas(ctx, nt):
+    """The merge kernel built for 128- and 256-thread CTAs, one CTA and several."""
+    ctx.set_cta_threads(nt)
+    try:
+        for s, n in enumerate([5, 65, 300, 1000, 2100]):
+            link = s % 4
+            D = synth.small_gmm(n, 300 + s) if s % 2 else synth.tie_heavy(n, 300 + s, levels=4)
+            want = oracle.cached(D, n, link)
+            for grid in (1, 3, 40):
+                _assert_same(_gpu(ctx, D, n, link, grid=grid), want, f"nt={nt} n={n} grid={grid}")
+    finally:
+        ctx.set_cta_threads(0)
+        ctx.set_grid(0)
+    with pytest.raises(LwError):
+        ctx.set_cta_threads(384)
+
+
 def test_gmm512_complete(ctx):
     """n = 512 points in R^8 from 8 Gaussians, complete linkage (default grid)."""
     w = synth.workload("gmm512")
