@@ -120,17 +120,19 @@ lw_status lw_wait(lw_ctx *ctx);
 /*
  * lw_get_stats -- counters of the last completed run, written to the host
  * array `stats` (first `count` entries; entries past the last counter are 0):
- *   [0] rows rescanned at once by their owner (cache emptied),
- *   [1] live cells read by those rescans,
+ *   [0] rounds (each certifies one or more consecutive merges between two
+ *       grid barriers),
+ *   [1] rounds that certified no merge (waiting for a row refill),
  *   [2] cells rewritten by the update formula (sum over merges of m_t - 2),
  *   [3] CTAs of the persistent grid,
  *   [4] row refills served by all CTAs together,
  *   [5] live cells read by those refills,
  *   [6] refills installed by the rows' owners,
  *   [8..13] with LW_OPT_PHASE_TIMES on: wall-clock nanoseconds summed over
- *       the CTAs of the grid, per phase of a merge: [8] barrier wait,
- *       [9] exchange + global minimum, [10] survivor row and refill
- *       installs, [11] update, [12] rescans + publish, [13] refill service.
+ *       the CTAs of the grid, per phase of a round: [8] barrier waits,
+ *       [9] exchange, walk and refill installs, [10] pass 1 (new cells, read
+ *       only), [11] refill service in the barrier window, [12] certification
+ *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish.
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 
@@ -174,7 +176,7 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
  * application's plug-in, or in a loop that must never enter the allocator.
  * It needs no lw_ctx and allocates nothing, host or device: the kernel's
  * scratch (cluster sizes, exchange records, barrier words) is a fixed
- * file-scope device array of 1 MB in liblw.so, created when the library is
+ * file-scope device array of 2 MB in liblw.so, created when the library is
  * loaded on a device and held by every device that loads it until the
  * process exits.
  *   dist, merges_out, heights_out  DEVICE pointers as for lw_cluster (dist is

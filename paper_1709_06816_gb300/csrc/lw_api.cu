@@ -159,12 +159,7 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     p.aligned16 = ((uintptr_t)ddist & 15u) == 0;
     p.merges = dmerges;
     p.heights = dheights;
-    p.size_g = reinterpret_cast<int *>(ws + L.size);
-    p.cand = reinterpret_cast<lw::Rec *>(ws + L.cand);
-    p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
-    p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
-    p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
-    p.status = reinterpret_cast<int *>(ws + L.status);
+    lw::bind_workspace(p, ws, L);
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
     p.skip_arrive_cta = (ctx->test_skip_arrive >= 0 && ctx->test_skip_arrive < G && G > 1)

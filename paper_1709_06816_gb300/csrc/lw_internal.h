@@ -10,23 +10,31 @@ namespace lw {
 constexpr int kThreads = 512;            // default threads per CTA of the merge kernel
 constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
 constexpr int kCacheKeys = 4;            // smallest keys cached per row
+constexpr int kPub = 4;                  // entries a CTA publishes per round
+constexpr int kRound = 16;               // most merges one round certifies
 constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
-constexpr int kMaxReq = 32;              // refill requests served per merge
-constexpr int kReqPerCta = 4;            // refill requests one CTA may make per merge
+constexpr int kMaxReq = 128;             // refill requests served per round
+constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
 constexpr int kStats = 16;
 constexpr uint64_t kNoKey = ~0ull;
+
+// Column word of a published entry: the column, or one of two stop marks.
+constexpr unsigned kColMask = 0x3fffffffu;
+constexpr unsigned kRowStop = 0x80000000u;   // the row's cache ends here (cells beyond unknown)
+constexpr unsigned kHardStop = 0x40000000u;  // the CTA published no entries beyond this one
 
 // Status words written by the kernel (values match lw_status).
 enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
 
-// One CTA's record for the next merge, 32 bytes: its candidate for the
-// global minimum, A = (bits(value) << 32) | row and c = column of its
-// smallest cell, and the rows (at most kReqPerCta) that ask for a refill.
-struct __align__(16) Rec {
-    unsigned long long A;
-    unsigned int c;
-    unsigned int nreq;
+// One CTA's record at the start of a round, 96 bytes: its kPub smallest
+// cache entries (key = (bits(value) << 32) | (row << 3) | rank, column word
+// beside it) and the rows (at most kReqPerCta) that ask for a refill.
+struct __align__(16) RecA {
+    unsigned long long key[kPub];
+    unsigned int col[kPub];
+    int nreq;
     int req[kReqPerCta];
+    int pad[3];
 };
 
 struct MergeParams {
@@ -38,9 +46,9 @@ struct MergeParams {
     int32_t *merges;               // [2(n-1)] device
     float *heights;                // [n-1]    device
     int *size_g;                   // [n] cluster sizes
-    Rec *cand;                     // [2][G] candidates (double-buffered by merge parity)
-    unsigned long long *islice;    // [2][G][kCacheKeys] survivor-row partial top-K
-    unsigned long long *parts;     // [3][G][kMaxReq][kCacheKeys] refill partial top-K
+    RecA *recA;                    // [G] published entries and refill requests
+    unsigned long long *recB;      // [G][2][kRound] per-pair minima of the new cells
+    unsigned long long *parts;     // [2][G][kMaxReq][kCacheKeys] refill partial top-K
     unsigned int *bar;             // grid barrier counter (zero at launch)
     int *status;                   // [4] status word [0]; barrier that gave up [1]
     long long *stats;              // [kStats] counters, see lw_get_stats
@@ -55,7 +63,7 @@ struct MergeParams {
 // block (every part 256-byte aligned).  The words from `zero` to `total`
 // (barrier, status, stats) must be zero at launch.
 struct WorkspaceLayout {
-    size_t size, cand, islice, parts, zero, bar, status, stats, total;
+    size_t size, recA, recB, parts, zero, bar, status, stats, total;
 };
 
 __host__ __device__ inline WorkspaceLayout workspace_layout(long long n, int G)
@@ -64,15 +72,26 @@ __host__ __device__ inline WorkspaceLayout workspace_layout(long long n, int G)
     WorkspaceLayout L;
     size_t off = 0;
     L.size = off;   off = up(off + sizeof(int) * (size_t)n);
-    L.cand = off;   off = up(off + sizeof(Rec) * 2 * (size_t)G);
-    L.islice = off; off = up(off + 8 * kCacheKeys * 2 * (size_t)G);
-    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 3 * (size_t)G);
+    L.recA = off;   off = up(off + sizeof(RecA) * (size_t)G);
+    L.recB = off;   off = up(off + 8 * 2 * kRound * (size_t)G);
+    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 2 * (size_t)G);
     L.zero = off;
     L.bar = off;    off = up(off + 256);
     L.status = off; off = up(off + 4 * sizeof(int));
     L.stats = off;  off = up(off + kStats * sizeof(long long));
     L.total = off;
     return L;
+}
+
+// Points p's scratch pointers into a workspace block laid out by L.
+__host__ __device__ inline void bind_workspace(MergeParams &p, char *ws, const WorkspaceLayout &L)
+{
+    p.size_g = reinterpret_cast<int *>(ws + L.size);
+    p.recA = reinterpret_cast<RecA *>(ws + L.recA);
+    p.recB = reinterpret_cast<unsigned long long *>(ws + L.recB);
+    p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
+    p.bar = reinterpret_cast<unsigned int *>(ws + L.bar);
+    p.status = reinterpret_cast<int *>(ws + L.status);
 }
 
 // One job of a batch (device table entry).

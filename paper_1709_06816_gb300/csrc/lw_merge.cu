@@ -5,38 +5,50 @@
 // spreads the packed upper triangle over MPI processes and exchanges local
 // minima and (i, j, distance) triples by messages (Section 5.3 steps 1-6b); on
 // one GB300 the whole triangle sits in HBM, so the "processors" become CTAs,
-// the broadcast of local minima becomes one 32-byte record per CTA read after
-// a grid barrier, and the triple exchange disappears: every CTA addresses row
-// and column i and j directly.
+// the broadcast of local minima becomes a small record per CTA read after a
+// grid barrier, and the triple exchange disappears: every CTA addresses rows
+// and columns i and j directly.
 //
 // Work split.  Rows are dealt to CTAs in blocks of 32 consecutive rows,
-// round-robin (block q -> CTA q mod G); a CTA "owns" those rows and, by the
-// same map, those columns.  The owner of row k
-//   - keeps, in shared memory, the kCacheKeys smallest keys of row k
-//     (key = (value bits << 32) | column, over live columns c > k) and a bound
-//     B: every live cell of the row outside the cache has a key above B
-//     (B = "none" when the cache holds every live cell of the row);
-//   - applies the update of Section 4 step 3 for k at every merge: reads D(k,i),
-//     D(k,j), writes D(k,i+j) into D(k,i), and maintains row k's cache
-//     (drops columns i and j, inserts the new cell (k,i) when it is <= B).
-// The row minimum is exact while the cache is not empty.  A row whose cache
-// runs low asks for a refill; in the barrier window of the NEXT merge (after
-// a CTA has arrived at the grid barrier and before it waits) one warp of
-// every CTA scans that CTA's columns of the row and publishes a partial
-// top-K list, and two merges after the request the owner merges the lists
-// and replays the two updates that happened meanwhile.  So row scans stay
-// off the critical path; only a row whose cache empties before its refill
-// lands is rescanned at once by its owner.
+// round-robin (block q -> CTA q mod G); a CTA "owns" those rows.  The owner
+// of row k keeps, in shared memory, the kCacheKeys smallest keys of row k
+// (key = (value bits << 32) | column, over live columns c > k) and a bound B:
+// every live cell of the row outside the cache has a key above B (B = "none"
+// when the cache holds every live cell of the row).
 //
-// The survivor row i is rewritten by every CTA (one cell per owned k > i);
-// each CTA folds its part of row i into its candidate and publishes its
-// partial top-K of row i, and the owner of i merges those lists after the
-// barrier.
+// Rounds.  A grid barrier costs about a microsecond on GB300, more than the
+// arithmetic of one merge, so the kernel certifies several consecutive merges
+// of the sequential iteration per pair of barriers.  The merges are exactly
+// those of the step-by-step algorithm (same pairs, same order, same rounded
+// values); only the bookkeeping differs.  One round:
 //
-// One grid barrier per merge:
-//   [wait] read G candidates (+ survivor lists, refill lists, requests)
-//   -> global minimum (value, i, j) -> emit step -> update + cache upkeep
-//   -> publish candidate and survivor list -> [arrive] serve refills [wait]
+//   A  every CTA publishes its kPub smallest cache entries, each row's
+//      entries followed by a stop mark at its bound B.  After the barrier
+//      every CTA walks the union of all published entries in (value, row,
+//      column) order and proposes a chain of disjoint pairs P_1..P_s: an
+//      entry whose row or column already belongs to a proposed pair is
+//      skipped, a stop mark of an untouched row (or the last entry of a CTA
+//      that had more) ends the walk.  P_{p+1} is then the smallest cell
+//      among those no earlier proposal touches.
+//   pass 1 (reads only): for every live k outside the chain and every pair a,
+//      the new distance D(k, i_a + j_a) of Section 4 step 3; each CTA
+//      publishes, per pair, its smallest new cell over all k and over k > i_a.
+//      The cells between members of two proposed pairs are computed by every
+//      CTA, in the order the sequential algorithm would write them.
+//   B  after the barrier, every CTA finds the longest prefix P_1..P_L such
+//      that each P_{p+1} is smaller than every cell the merges P_1..P_p have
+//      rewritten: then P_{p+1} is the global minimum after merge p, so the
+//      prefix is what the sequential algorithm does.  P_1 always qualifies.
+//   pass 2: the L merges are emitted and applied: D(k, i_a) rewritten, caches
+//      kept (column j_a leaves, the new cell (k, i_a) enters when <= B), the
+//      survivor rows get their new caches from the published minima.
+//
+// A row whose cache runs low asks for a refill; in the window of the next
+// round's barrier B (after a CTA has arrived and before it waits) one warp of
+// every CTA scans that CTA's columns of the row and publishes a partial top-K
+// list; at the start of the round after that the owner merges the lists and
+// replays the merges of the round in between.  Rows scans stay off the
+// critical path.
 //
 // Exact arithmetic: every product and sum of the update uses __fmul_rn /
 // __fadd_rn / __fsub_rn (never contracted into FMA), the coefficient
@@ -182,59 +194,108 @@ __device__ __forceinline__ void cand_min(Cand &x, const Cand &y)
         x = y;
 }
 
-// Warp-wide lexicographic minimum of (value bits, row, column) with three
-// hardware warp reductions, each over the lanes that tie on the words before.
-__device__ __forceinline__ Cand warp_cand_min(Cand v)
+constexpr int S = kRound;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr u64 kHi = 0xffffffff00000000ull;
+static_assert(kPub == K, "a CTA publishes its entries with the K-list reductions");
+static_assert(K == 4, "sort_list is a 4-input network");
+static_assert(S <= 32 && (32 % S) == 0, "pair minima are reduced across lanes in groups of S");
+
+// Sort a K-list in which any entries were replaced by kNoKey.
+__device__ __forceinline__ void sort_list(u64 (&L)[K])
 {
-    const unsigned h = (unsigned)(v.A >> 32), r = (unsigned)v.A;
-    const unsigned mh = __reduce_min_sync(0xffffffffu, h);
-    const unsigned mr = __reduce_min_sync(0xffffffffu, h == mh ? r : 0xffffffffu);
-    const unsigned mc =
-        __reduce_min_sync(0xffffffffu, (h == mh && r == mr) ? v.c : 0xffffffffu);
-    Cand out;
-    out.A = ((u64)mh << 32) | mr;
-    out.c = mc;
-    return out;
+    cswap(L[0], L[1]);
+    cswap(L[2], L[3]);
+    cswap(L[0], L[2]);
+    cswap(L[1], L[3]);
+    cswap(L[1], L[2]);
+}
+
+// The update of Section 4 step 3 with the Table 1 coefficients for clusters
+// of sizes ni, nj (merged) and nk (the other one); terms added in printed
+// order, every operation rounded once.
+__device__ __forceinline__ float lw_cell(int linkage, float dki, float dkj, float dij, int ni, int nj,
+                                         int nk)
+{
+    float ai = 0.5f, aj = 0.5f, be = 0.0f, ga = 0.0f;
+    if (linkage == 0) {
+        ga = -0.5f;
+    } else if (linkage == 1) {
+        ga = 0.5f;
+    } else if (linkage == 2) {
+        const float sum = (float)(ni + nj);
+        ai = __fdiv_rn((float)ni, sum);
+        aj = __fdiv_rn((float)nj, sum);
+    } else {
+        const float T = (float)(ni + nj + nk);
+        ai = __fdiv_rn((float)(ni + nk), T);
+        aj = __fdiv_rn((float)(nj + nk), T);
+        be = -__fdiv_rn((float)nk, T);
+    }
+    float s = __fmul_rn(ai, dki);
+    s = __fadd_rn(s, __fmul_rn(aj, dkj));
+    s = __fadd_rn(s, __fmul_rn(be, dij));
+    s = __fadd_rn(s, __fmul_rn(ga, fabsf(__fsub_rn(dki, dkj))));
+    return s;
+}
+
+// Order key of the cell between clusters x and y holding value bits vb.
+__device__ __forceinline__ Cand cell_cand(unsigned vb, unsigned x, unsigned y)
+{
+    Cand c;
+    c.A = ((u64)vb << 32) | (x < y ? x : y);
+    c.c = x < y ? y : x;
+    return c;
 }
 
 template <int NT>
 struct Shared {
-    Cand red[(NT / 32) + 1];
-    u64 tk[(NT / 32)][K];
+    static constexpr int W = NT / 32;
+    u64 tk[W][K];
     u64 tko[K];
-    int wcnt[(NT / 32)];        // per-warp request counts (prefix sums)
+    int wcnt[W];
     int flag;
-    int nresc;               // rows to rescan at once this merge
-    int nexec;               // refill rows served this merge
+    int nexec;                   // refill rows served this round
     int exec_row[kMaxReq];
-    int my_off;              // where this CTA's requests landed in the list
-    int nmyreq[2];           // this CTA's requests, by merge parity
+    int my_off;                  // where this CTA's requests landed in the list
+    int nmyreq[2];               // this CTA's requests, by round parity
     int myreq_l[2][kReqPerCta];
-    int ninst;               // refills to install at the start of the next merge
-    int inst_slot[kMaxReq];  // owned slots of those rows
+    int ninst;                   // refills to install at the start of the next round
+    int inst_slot[kReqPerCta];
+    // the round's chain of proposed merges and the cells between its members
+    int np, nacc;
+    int pi[S], pj[S];
+    float ph[S];
+    int szi[S], szj[S];
+    u64 amin[S], hmin[S];        // this CTA's smallest new cell per pair (all k, k > i)
+    u64 gamin[S], ghmin[S];      // the same over all CTAs
+    float Dm[2 * S][2 * S];      // D between members (2a = i_a, 2a + 1 = j_a)
+    float X[S][S];               // cell (i_a, i_b) after merge a alone
+    float Y[S][S];               // cell (i_a, j_b) after merge a alone
+    float C[S][S];               // cell (i_a, i_b) after merges a then b (a < b)
+    // the previous round's merges, replayed on installed refills
+    int ppi[S], ppj[S];
+    int nprev;
 };
 
-// After the barrier: the global minimum over the G candidates, and the list
-// of rows to refill in this merge -- every CTA's requests in CTA order
-// (deterministic, the same in every CTA), cut at kMaxReq.  Thread t holds
-// CTA t's record (cnt requests in rq).  Sets sh.exec_row, sh.nexec and
-// sh.my_off (the position of this CTA's first request).
+// After barrier A: the list of rows to refill in this round -- every CTA's
+// requests in CTA order (deterministic, the same in every CTA), cut at
+// kMaxReq.  Thread t holds CTA t's request count and rows.  Sets
+// sh.exec_row, sh.nexec and sh.my_off (the position of this CTA's first
+// request).
 template <int NT>
-__device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh)
+__device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = cnt;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, inc, off);
+        const int o = __shfl_up_sync(kFull, inc, off);
         if (lane >= off)
             inc += o;
     }
-    v = warp_cand_min(v);
     if (lane == 31)
         sh.wcnt[warp] = inc;
-    if (lane == 0)
-        sh.red[warp] = v;
     __syncthreads();
     int base = 0;
     for (int w = 0; w < warp; ++w)
@@ -248,41 +309,14 @@ __device__ Cand exchange_reduce(Cand v, int cnt, const int (&rq)[kReqPerCta], in
     if ((int)threadIdx.x == b)
         sh.my_off = off0;
     if (warp == 0) {
-        Cand w = {kNoKey, 0xffffffffu};
-        if (lane < (NT / 32))
-            w = sh.red[lane];
-        w = warp_cand_min(w);
         int tot = lane < (NT / 32) ? sh.wcnt[lane] : 0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
-            tot += __shfl_xor_sync(0xffffffffu, tot, off);
-        if (lane == 0) {
-            sh.red[(NT / 32)] = w;
-            sh.nexec = tot < kMaxReq ? tot : kMaxReq;
-        }
-    }
-    __syncthreads();
-    return sh.red[(NT / 32)];
-}
-
-template <int NT>
-__device__ Cand block_cand_min(Cand v, Shared<NT> &sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_cand_min(v);
-    if (lane == 0)
-        sh.red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        Cand w = {kNoKey, 0xffffffffu};
-        if (lane < (NT / 32))
-            w = sh.red[lane];
-        w = warp_cand_min(w);
+            tot += __shfl_xor_sync(kFull, tot, off);
         if (lane == 0)
-            sh.red[(NT / 32)] = w;
+            sh.nexec = tot < kMaxReq ? tot : kMaxReq;
     }
     __syncthreads();
-    return sh.red[(NT / 32)];
 }
 
 // K smallest keys over every thread's list; result in sh.tko (all threads).
@@ -305,42 +339,6 @@ __device__ void block_topk(u64 (&L)[K], Shared<NT> &sh)
             M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
         warp_topk(M, w);
         if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                sh.tko[q] = w[q];
-        }
-    }
-    __syncthreads();
-}
-
-// Both reductions a CTA publishes, in one pass: the candidate minimum (in
-// sh.red[(NT / 32)]) and the K smallest survivor-row keys (in sh.tko).
-template <int NT>
-__device__ void block_publish(Cand c, u64 (&L)[K], Shared<NT> &sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u64 w[K];
-    warp_topk(L, w);
-    c = warp_cand_min(c);
-    if (lane == 0) {
-        sh.red[warp] = c;
-#pragma unroll
-        for (int q = 0; q < K; ++q)
-            sh.tk[warp][q] = w[q];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        Cand x = {kNoKey, 0xffffffffu};
-        u64 M[K];
-#pragma unroll
-        for (int q = 0; q < K; ++q)
-            M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
-        if (lane < (NT / 32))
-            x = sh.red[lane];
-        warp_topk(M, w);
-        x = warp_cand_min(x);
-        if (lane == 0) {
-            sh.red[(NT / 32)] = x;
 #pragma unroll
             for (int q = 0; q < K; ++q)
                 sh.tko[q] = w[q];
@@ -470,56 +468,13 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
     warp_topk(L, out);
 }
 
-// K smallest keys of row r over live columns, computed by the whole CTA
-// (for a row whose cache empties before its refill arrives).  Adds the live
-// cells read to `live_cells`.  Result in sh.tko.
-template <int NT>
-__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT> &sh,
-                               long long &live_cells)
-{
-    const long long n = p.n;
-    const long long start = tri_off(r, n);
-    const long long end = start + (n - r - 1);
-    const long long base_c = r + 1 - start;
-    u64 L[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-        L[q] = kNoKey;
-    long long cnt = 0;
-    for (long long q = start + threadIdx.x; q < end; q += NT) {
-        const long long c = q + base_c;
-        if (live(bitmap, c)) {
-            list_insert(L, make_key(__ldcg(p.D + q), (unsigned)c));
-            ++cnt;
-        }
-    }
-    live_cells += cnt;
-    block_topk(L, sh);
-}
-
-__device__ __forceinline__ void load_list(u64 (&L)[K], const u64 *src)
-{
-    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
-#pragma unroll
-    for (int q = 0; q < K / 2; ++q) {
-        const ulonglong2 v = __ldcg(s2 + q);
-        L[2 * q] = v.x;
-        L[2 * q + 1] = v.y;
-    }
-}
-
-__device__ __forceinline__ void publish_list(u64 *dst, const u64 *src, int tid)
-{
-    if (tid < K / 2)
-        __stcg(reinterpret_cast<ulonglong2 *>(dst) + tid, make_ulonglong2(src[2 * tid], src[2 * tid + 1]));
-}
-
 // All n - 1 merges of one job, run by CTA b of the job's G CTAs (every CTA
 // of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
 // bytes of dynamic shared memory.
 template <int NT>
 __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared<NT> &sh)
 {
+    constexpr int W = NT / 32;
     const long long n = p.n;
     const int G = p.G;
     const int tid = threadIdx.x;
@@ -530,20 +485,29 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
 
-    // dynamic shared memory: liveness bitmap, then per owned slot l: cache
+    // dynamic shared memory: liveness bitmap; the published entries of every
+    // CTA (keys, column words, walk positions); then per owned slot l: cache
     // keys (key q of slot l at ck[q * Rmax + l]: consecutive threads read
-    // consecutive words), bound, the new key of cell (k, i) of the last two
-    // merges (by merge parity), size, key count, pending refill (merge, list
-    // position), and the list of rows to rescan at once
-    unsigned *bitmap = reinterpret_cast<unsigned *>(smem_raw);
-    u64 *ck = reinterpret_cast<u64 *>(smem_raw + ((nwords * 4 + 15) & ~15LL));
-    u64 *cB = ck + Rmax * K;
-    u64 *upd = cB + Rmax;  // [2][Rmax]
-    int *rsize = reinterpret_cast<int *>(upd + 2 * Rmax);
+    // consecutive words), bound, size, key count, pending refill (round,
+    // list position) and a flag for rows in this round's chain
+    unsigned char *q0 = smem_raw;
+    unsigned *bitmap = reinterpret_cast<unsigned *>(q0);
+    q0 += (nwords * 4 + 15) & ~15LL;
+    u64 *wkey = reinterpret_cast<u64 *>(q0);
+    q0 += (size_t)G * K * 8;
+    u64 *ck = reinterpret_cast<u64 *>(q0);
+    q0 += (size_t)Rmax * K * 8;
+    u64 *cB = reinterpret_cast<u64 *>(q0);
+    q0 += (size_t)Rmax * 8;
+    unsigned *wcol = reinterpret_cast<unsigned *>(q0);
+    q0 += (size_t)G * K * 4;
+    int *hd = reinterpret_cast<int *>(q0);
+    q0 += ((size_t)G * 4 + 15) & ~(size_t)15;
+    int *rsize = reinterpret_cast<int *>(q0);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
     int *pend_s = pend_t + Rmax;
-    int *rlist = pend_s + Rmax;
+    unsigned char *mflag = reinterpret_cast<unsigned char *>(pend_s + Rmax);
 
     auto row_of = [&](int l) -> long long {
         return (long long)((long long)b + (long long)G * (l >> 5)) * kRowBlock + (l & 31);
@@ -562,6 +526,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         for (int q = 0; q < K; ++q)
             ck[(size_t)q * Rmax + l] = L[q];
     };
+    // a refill request for slot l in round r (list par = r & 1)
+    auto request = [&](int l, int r) {
+        const int par = r & 1;
+        const int q = atomicAdd(&sh.nmyreq[par], 1);
+        if (q < kReqPerCta) {
+            sh.myreq_l[par][q] = l;
+            pend_t[l] = r;
+        }
+    };
 
     // per-phase wall-clock totals of this CTA (thread 0), when timing is on
     u64 ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
@@ -574,6 +547,73 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
     };
 
+    long long st_updates = 0, st_fill_cells = 0;
+    long long st_fills = 0, st_installs = 0, st_rounds = 0, st_idle = 0;
+
+    // The records of round rr: this CTA's kPub smallest entries (cached keys
+    // and bound marks of its rows) and its refill requests of round rr - 1.
+    // Also lists the refills to install in round rr (served in round rr - 1).
+    auto publish = [&](int rr) {
+        u64 Lst[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            Lst[q] = kNoKey;
+        for (int l = tid; l < R; l += NT) {
+            const int c = ccnt[l];
+            const u64 B = cB[l];
+            if (c > 0 || B != kNoKey) {
+                const u64 rowbits = (u64)row_of(l) << 3;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    if (q < c)
+                        list_insert(Lst, (ck[(size_t)q * Rmax + l] & kHi) | rowbits | (u64)q);
+                }
+                if (B != kNoKey)
+                    list_insert(Lst, (B & kHi) | rowbits | (u64)c);
+            }
+            if (rr >= 2 && pend_t[l] == rr - 2) {
+                const int s2 = atomicAdd(&sh.ninst, 1);
+                sh.inst_slot[s2] = l;
+            }
+        }
+        block_topk(Lst, sh);
+        if (tid == 0) {
+            unsigned cols[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const u64 key = sh.tko[q];
+                unsigned col = 0;
+                if (key != kNoKey) {
+                    const unsigned lo = (unsigned)key;
+                    const int slot = slot_of((long long)(lo >> 3));
+                    const int rank = (int)(lo & 7u);
+                    col = rank < ccnt[slot] ? (unsigned)ck[(size_t)rank * Rmax + slot] : kRowStop;
+                    if (q == K - 1)
+                        col |= kHardStop;  // more entries may follow: none is published
+                }
+                cols[q] = col;
+            }
+            const int par = (rr - 1) & 1;
+            int nq = rr >= 1 ? sh.nmyreq[par] : 0;
+            nq = nq < kReqPerCta ? nq : kReqPerCta;
+            if (rr >= 1)
+                sh.nmyreq[par] = nq;
+            int rows[kReqPerCta];
+#pragma unroll
+            for (int q = 0; q < kReqPerCta; ++q)
+                rows[q] = q < nq ? (int)row_of(sh.myreq_l[par][q]) : -1;
+            uint4 *dst = reinterpret_cast<uint4 *>(p.recA + b);
+            __stcg(dst + 0, make_uint4((unsigned)sh.tko[0], (unsigned)(sh.tko[0] >> 32),
+                                       (unsigned)sh.tko[1], (unsigned)(sh.tko[1] >> 32)));
+            __stcg(dst + 1, make_uint4((unsigned)sh.tko[2], (unsigned)(sh.tko[2] >> 32),
+                                       (unsigned)sh.tko[3], (unsigned)(sh.tko[3] >> 32)));
+            __stcg(dst + 2, make_uint4(cols[0], cols[1], cols[2], cols[3]));
+            __stcg(dst + 3, make_uint4((unsigned)nq, (unsigned)rows[0], (unsigned)rows[1], (unsigned)rows[2]));
+            __stcg(dst + 4, make_uint4((unsigned)rows[3], (unsigned)rows[4], (unsigned)rows[5], (unsigned)rows[6]));
+            __stcg(dst + 5, make_uint4((unsigned)rows[7], 0u, 0u, 0u));
+        }
+    };
+
     // ---- setup
     for (long long w = tid; w < nwords; w += NT) {
         const long long live_n = n - w * 32;
@@ -582,17 +622,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     for (int l = tid; l < R; l += NT) {
         rsize[l] = 1;
         pend_t[l] = -1;
-        upd[l] = kNoKey;
-        upd[Rmax + l] = kNoKey;
+        mflag[l] = 0;
     }
     for (long long r = (long long)b * NT + tid; r < n; r += (long long)G * NT)
         p.size_g[r] = 1;
     if (tid == 0) {
-        sh.nresc = 0;
         sh.ninst = 0;
         sh.nexec = 0;
         sh.nmyreq[0] = 0;
         sh.nmyreq[1] = 0;
+        sh.nprev = 0;
     }
 
     // ---- phase 0: validate the matrix and fill the caches of owned rows
@@ -600,7 +639,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     // triangle, so every CTA reads about the same number of cells)
     {
         int bad = 0;
-        for (int l = warp; l < R; l += (NT / 32)) {
+        for (int l = warp; l < R; l += W) {
             const long long r = row_of(l);
             u64 top[K];
 #pragma unroll
@@ -619,27 +658,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             atomicCAS(p.status, 0, kErrInput);
     }
     __syncthreads();
+    publish(0);
 
-    long long st_updates = 0, st_resc_cells = 0, st_fill_cells = 0;
-    long long st_rescans = 0, st_fills = 0, st_installs = 0;
-
-    // first records: each CTA's smallest cached key, no refill requests
-    {
-        Cand c = {kNoKey, 0xffffffffu};
-        for (int l = tid; l < R; l += NT) {
-            if (ccnt[l] > 0) {
-                const u64 k = ck[l];
-                Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
-                cand_min(c, o);
-            }
-        }
-        c = block_cand_min(c, sh);
-        if (tid == 0) {
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + b);
-            __stcg(dst, make_ulonglong2(c.A, (u64)c.c));
-            __stcg(dst + 1, make_ulonglong2(0ull, 0ull));
-        }
-    }
     unsigned epoch = 0;
     if (b == p.skip_arrive_cta)
         return;
@@ -654,62 +674,54 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     if (p.timing && tid == 0)
         tmark = global_ns();
 
-    // the pair merged in merge t-1
-    long long i1 = -1, j1 = -1;
-    int carried = 0;  // size of the cluster in slot i1 after merge t-1
-
-    for (long long t = 0; t < n - 1; ++t) {
-        const int par = (int)(t & 1);
-
-        // ---- exchange: every CTA's record (candidate + refill requests),
-        // the survivor row's partial lists, the first refill to install --
-        // one round of loads, then one reduction
-        const bool own_prev = i1 >= 0 && owner_of(i1) == b;
-        const int ninst = sh.ninst;
-        const int pbuf = (int)((t + 1) % 3);  // refills served two merges ago
-        Cand mine = {kNoKey, 0xffffffffu};
-        int rcnt = 0;
-        int rq[kReqPerCta];
-#pragma unroll
-        for (int q = 0; q < kReqPerCta; ++q)
-            rq[q] = -1;
-        u64 sl[K], il0[K];
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-            sl[q] = kNoKey;
-            il0[q] = kNoKey;
-        }
-        if (tid < G) {
-            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.cand + par * G + tid);
-            const ulonglong2 w0 = __ldcg(src);
-            const ulonglong2 w1 = __ldcg(src + 1);
-            mine.A = w0.x;
-            mine.c = (unsigned)w0.y;
-            rcnt = (int)(w0.y >> 32);
-            rq[0] = (int)(unsigned)w1.x;
-            rq[1] = (int)(unsigned)(w1.x >> 32);
-            rq[2] = (int)(unsigned)w1.y;
-            rq[3] = (int)(unsigned)(w1.y >> 32);
-            if (own_prev)
-                load_list(sl, p.islice + ((size_t)par * G + tid) * K);
-            if (ninst > 0)
-                load_list(il0, p.parts + (((size_t)pbuf * G + tid) * kMaxReq +
-                                          pend_s[sh.inst_slot[0]]) * K);
-        }
-        const Cand best = exchange_reduce(mine, rcnt, rq, b, sh);
-        const long long i = (long long)(best.A & 0xffffffffull);
-        const long long j = (long long)best.c;
-        const float h = __uint_as_float((unsigned)(best.A >> 32));
-        // every CTA read the same records, so every CTA takes this exit together
-        if (i >= n || j >= n || i >= j) {
+    long long t = 0;   // merges done
+    const long long max_rounds = 2 * n + 64;
+    for (int r = 0;; ++r) {
+        const int par = r & 1;
+        if (r > max_rounds) {
+            // no progress: a stop mark that no refill lifts (every CTA sees the
+            // same count and leaves here together)
             if (tid == 0)
                 atomicCAS(p.status, 0, kErrInternal);
             return;
         }
-        // this CTA's requests of merge t-1 now have list positions
+
+        // ---- A: every CTA's published entries and refill requests
+        {
+            int rcnt = 0;
+            int rq[kReqPerCta];
+#pragma unroll
+            for (int q = 0; q < kReqPerCta; ++q)
+                rq[q] = -1;
+            if (tid < G) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.recA + tid);
+                const uint4 w0 = __ldcg(src), w1 = __ldcg(src + 1), w2 = __ldcg(src + 2);
+                const uint4 w3 = __ldcg(src + 3), w4 = __ldcg(src + 4), w5 = __ldcg(src + 5);
+                wkey[tid * K + 0] = ((u64)w0.y << 32) | w0.x;
+                wkey[tid * K + 1] = ((u64)w0.w << 32) | w0.z;
+                wkey[tid * K + 2] = ((u64)w1.y << 32) | w1.x;
+                wkey[tid * K + 3] = ((u64)w1.w << 32) | w1.z;
+                wcol[tid * K + 0] = w2.x;
+                wcol[tid * K + 1] = w2.y;
+                wcol[tid * K + 2] = w2.z;
+                wcol[tid * K + 3] = w2.w;
+                hd[tid] = 0;
+                rcnt = (int)w3.x;
+                rq[0] = (int)w3.y;
+                rq[1] = (int)w3.z;
+                rq[2] = (int)w3.w;
+                rq[3] = (int)w4.x;
+                rq[4] = (int)w4.y;
+                rq[5] = (int)w4.z;
+                rq[6] = (int)w4.w;
+                rq[7] = (int)w5.x;
+            }
+            exchange_requests(rcnt, rq, b, sh);
+        }
+        // this CTA's requests of round r - 1 now have list positions
         {
             const int pq = par ^ 1;
-            const int nmy = sh.nmyreq[pq];
+            const int nmy = r >= 1 ? sh.nmyreq[pq] : 0;
             if (tid < nmy) {
                 const int l = sh.myreq_l[pq][tid];
                 const int pos = sh.my_off + tid;
@@ -719,286 +731,267 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     pend_t[l] = -1;  // not served: the row may ask again
             }
         }
+        __syncthreads();
+        if (tid == 0)
+            sh.nmyreq[par] = 0;
         lap(ph1);
 
-        // survivor of the previous merge: merge the G partial lists of its row
-        if (own_prev) {
-            block_topk(sl, sh);
-            if (tid == 0) {
-                const int l = slot_of(i1);
-                cache_store(l, sh.tko);
-                const int c = list_count(sh.tko);
-                ccnt[l] = c;
-                cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
-                __stcg(p.size_g + i1, carried);  // deferred size write
-            }
-        }
-
-        // refills served two merges ago (in the barrier window of merge t-2):
-        // merge the partial lists, then replay merges t-2 and t-1 on the row:
-        // the served scan left out column i of merge t-2 and may have seen
-        // either value of the cells merge t-1 touched
-        for (int s = 0; s < ninst; ++s) {
-            const int l = sh.inst_slot[s];
-            u64 L[K];
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                L[q] = il0[q];
-            if (s > 0) {
-#pragma unroll
-                for (int q = 0; q < K; ++q)
-                    L[q] = kNoKey;
-                if (tid < G)
-                    load_list(L, p.parts + (((size_t)pbuf * G + tid) * kMaxReq + pend_s[l]) * K);
-            }
-            block_topk(L, sh);
-            if (tid == 0) {
-                u64 M[K];
-#pragma unroll
-                for (int q = 0; q < K; ++q)
-                    M[q] = sh.tko[q];
-                int c = list_count(M);
-                u64 B = c == K ? M[K - 1] : kNoKey;
-                // merge t-2: the new cell (r, i_{t-2})
-                u64 x = upd[(size_t)par * Rmax + l];
-                if (x != kNoKey && x <= B) {
-                    list_insert(M, x);
-                    if (c == K)
-                        B = M[K - 1];
-                    else
-                        ++c;
-                }
-                // merge t-1: column j1 left, cell (r, i1) changed
-#pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const unsigned col = (unsigned)M[q];
-                    if (M[q] != kNoKey && (col == (unsigned)i1 || col == (unsigned)j1))
-                        M[q] = kNoKey;
-                }
-                close_holes(M);
-                c = list_count(M);
-                x = upd[(size_t)(par ^ 1) * Rmax + l];
-                if (x != kNoKey && x <= B) {
-                    list_insert(M, x);
-                    if (c == K)
-                        B = M[K - 1];
-                    else
-                        ++c;
-                }
-                cache_store(l, M);
-                ccnt[l] = c;
-                cB[l] = B;
-                pend_t[l] = -1;
-                if (c == 0 && B != kNoKey) {
-                    // every cached key left: rescan the row after the update
-                    rlist[atomicAdd(&sh.nresc, 1)] = l;
-                    pend_t[l] = -2;
+        if (warp == 0) {
+            // ---- the walk: merge the G published lists in key order
+            u64 lm = kNoKey;
+            int lg = -1;
+            for (int g = lane; g < G; g += 32) {
+                const u64 k0 = wkey[g * K];
+                if (k0 < lm) {
+                    lm = k0;
+                    lg = g;
                 }
             }
-        }
-        st_installs += ninst;
-
-        if (tid == 0) {
-            if (b == 0) {
-                p.merges[2 * t] = (int32_t)i;
-                p.merges[2 * t + 1] = (int32_t)j;
-                p.heights[t] = h;
-            }
-            bitmap[j >> 5] &= ~(1u << (j & 31));  // Section 4 step 2: slot j retires
-            sh.ninst = 0;
-            sh.nmyreq[par] = 0;
-        }
-        int ni = 1, nj = 1;
-        if (p.linkage >= 2) {
-            ni = (i == i1) ? carried : __ldcg(p.size_g + i);
-            nj = (j == i1) ? carried : __ldcg(p.size_g + j);
-        }
-        __syncthreads();
-        lap(ph2);
-
-        // ---- Section 4 step 3: D(k, i+j) for every live k owned here
-        float ai = 0.5f, aj = 0.5f, be = 0.0f, ga = 0.0f;
-        if (p.linkage == 0) {
-            ga = -0.5f;
-        } else if (p.linkage == 1) {
-            ga = 0.5f;
-        } else if (p.linkage == 2) {
-            const float sum = (float)(ni + nj);
-            ai = __fdiv_rn((float)ni, sum);
-            aj = __fdiv_rn((float)nj, sum);
-        }
-        u64 il[K];  // this thread's smallest new cells of the survivor row
-#pragma unroll
-        for (int q = 0; q < K; ++q)
-            il[q] = kNoKey;
-        u64 *updt = upd + (size_t)par * Rmax;
-        for (int l = tid; l < R; l += NT) {
-            const long long k = row_of(l);
-            if (k >= n || k == i || k == j || !live(bitmap, k))
-                continue;
-            const long long pki = pair_idx(k, i, n);
-            const long long pkj = pair_idx(k, j, n);
-            const float a = __ldcg(p.D + pki);
-            const float bb = __ldcg(p.D + pkj);
-            if (p.linkage == 3) {
-                const int nk = rsize[l];
-                const float T = (float)(ni + nj + nk);
-                ai = __fdiv_rn((float)(ni + nk), T);
-                aj = __fdiv_rn((float)(nj + nk), T);
-                be = -__fdiv_rn((float)nk, T);
-            }
-            float s = __fmul_rn(ai, a);
-            s = __fadd_rn(s, __fmul_rn(aj, bb));
-            s = __fadd_rn(s, __fmul_rn(be, h));
-            s = __fadd_rn(s, __fmul_rn(ga, fabsf(__fsub_rn(a, bb))));
-            __stcg(p.D + pki, s);
-            ++st_updates;
-            if (k > i) {
-                // cell (i,k) belongs to the survivor row i
-                list_insert(il, make_key(s, (unsigned)k));
-                updt[l] = kNoKey;
-                if (k > j)
-                    continue;  // row k holds neither column i nor column j
-            }
-            // row k loses column j; if k < i its cell (k,i) changed as well
-            u64 C[K];
-            cache_load(C, l);
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const unsigned col = (unsigned)C[q];
-                if (col == (unsigned)j || (k < i && col == (unsigned)i))
-                    C[q] = kNoKey;
-            }
-            close_holes(C);
-            int c = list_count(C);
-            u64 B = cB[l];
-            if (k < i) {
-                const u64 x = make_key(s, (unsigned)i);
-                updt[l] = x;
-                if (x <= B) {
-                    list_insert(C, x);
-                    if (c == K)
-                        B = C[K - 1];
-                    else
-                        ++c;
+            int np = 0;
+            int member = -1;  // lane 2a holds i_a, lane 2a + 1 holds j_a
+            for (int guard = 0; guard <= G * K; ++guard) {
+                const u64 m = warp_u64_min(lm);
+                if (m == kNoKey)
+                    break;
+                const int src = __ffs(__ballot_sync(kFull, lm == m)) - 1;
+                unsigned col = 0;
+                if (lane == src) {
+                    const int h = hd[lg];
+                    col = wcol[lg * K + h];
+                    hd[lg] = h + 1;
+                    lm = kNoKey;
+                    lg = -1;
+                    for (int g = lane; g < G; g += 32) {
+                        const int hh = hd[g];
+                        if (hh < K) {
+                            const u64 kk = wkey[g * K + hh];
+                            if (kk < lm) {
+                                lm = kk;
+                                lg = g;
+                            }
+                        }
+                    }
                 }
-            }
-            cache_store(l, C);
-            ccnt[l] = c;
-            cB[l] = B;
-            if (c == 0 && B != kNoKey) {
-                // live cells remain but none is cached: rescan (once)
-                if (pend_t[l] != -2)
-                    rlist[atomicAdd(&sh.nresc, 1)] = l;
-                pend_t[l] = -2;
-            } else if (c <= kRefillAt && B != kNoKey && pend_t[l] < 0) {
-                // (a cache that holds every live cell of its row needs no refill)
-                const int q = atomicAdd(&sh.nmyreq[par], 1);
-                if (q < kReqPerCta) {
-                    sh.myreq_l[par][q] = l;
-                    pend_t[l] = (int)t;
+                col = __shfl_sync(kFull, col, src);
+                const int row = (int)(((unsigned)m) >> 3);
+                bool stop = (col & kHardStop) != 0;
+                if (!__any_sync(kFull, member == row)) {
+                    if (col & kRowStop) {
+                        stop = true;  // the row's smallest untouched cell is unknown
+                    } else {
+                        const int c = (int)(col & kColMask);
+                        if (!__any_sync(kFull, member == c)) {
+                            if (lane == 2 * np)
+                                member = row;
+                            if (lane == 2 * np + 1)
+                                member = c;
+                            if (lane == 0) {
+                                sh.pi[np] = row;
+                                sh.pj[np] = c;
+                                sh.ph[np] = __uint_as_float((unsigned)(m >> 32));
+                            }
+                            ++np;
+                            if (np == S)
+                                stop = true;
+                        }
+                    }
                 }
+                if (stop)
+                    break;
             }
-        }
-        if (tid == 0) {
-            if (owner_of(j) == b) {
-                const int l = slot_of(j);
-                ccnt[l] = 0;
-                pend_t[l] = -1;
-            }
-            if (owner_of(i) == b) {
-                const int l = slot_of(i);
-                ccnt[l] = 0;  // rebuilt from the partial lists after the barrier
-                pend_t[l] = -1;
-                rsize[l] = ni + nj;
-            }
-        }
-        __syncthreads();
-        lap(ph3);
-
-        // ---- rows whose cache emptied before a refill arrived
-        const int nresc = sh.nresc;
-        for (int q = 0; q < nresc; ++q) {
-            const int l = rlist[q];
-            block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
-            if (tid == 0) {
-                cache_store(l, sh.tko);
-                const int c = list_count(sh.tko);
-                ccnt[l] = c;
-                cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
-                pend_t[l] = -1;
-            }
-        }
-        st_rescans += nresc;
-        if (nresc > 0)
-            __syncthreads();  // the rescanned caches (written by thread 0) before anyone reads them
-
-        // ---- publish: this CTA's candidate, its refill requests and its
-        // part of the survivor row
-        {
-            Cand c = {kNoKey, 0xffffffffu};
-            for (int l = tid; l < R; l += NT) {
-                if (ccnt[l] > 0) {
-                    const u64 k = ck[l];
-                    Cand o = {(k & 0xffffffff00000000ull) | (u64)row_of(l), (unsigned)k};
-                    cand_min(c, o);
-                }
-                // a refill asked for in merge t-2 was served in the barrier
-                // window of merge t-1 and is installed at merge t+1 (pend_t
-                // is negative when no refill is pending)
-                if (t >= 2 && pend_t[l] == (int)t - 2) {
-                    const int s = atomicAdd(&sh.ninst, 1);
-                    sh.inst_slot[s] = l;
-                }
-            }
-            block_publish(c, il, sh);
-            if (tid == 0) {
-                Cand x = sh.red[(NT / 32)];
-                const u64 h0 = sh.tko[0];
-                if (h0 != kNoKey) {
-                    const Cand o = {(h0 & 0xffffffff00000000ull) | (u64)i, (unsigned)h0};
-                    cand_min(x, o);
-                }
-                int nq = sh.nmyreq[par];
-                nq = nq < kReqPerCta ? nq : kReqPerCta;
-                sh.nmyreq[par] = nq;
-                unsigned rr[kReqPerCta];
-#pragma unroll
-                for (int q = 0; q < kReqPerCta; ++q)
-                    rr[q] = q < nq ? (unsigned)row_of(sh.myreq_l[par][q]) : 0xffffffffu;
-                ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.cand + (par ^ 1) * G + b);
-                __stcg(dst, make_ulonglong2(x.A, (u64)x.c | ((u64)nq << 32)));
-                __stcg(dst + 1, make_ulonglong2((u64)rr[0] | ((u64)rr[1] << 32),
-                                                (u64)rr[2] | ((u64)rr[3] << 32)));
-                sh.nresc = 0;
-            }
-            publish_list(p.islice + ((size_t)(par ^ 1) * G + b) * K, sh.tko, tid);
-        }
-        lap(ph4);
-        i1 = i;
-        j1 = j;
-        carried = ni + nj;
-        if (t + 2 >= n)
-            break;  // that was the last merge
-        grid_arrive(p, epoch);
-
-        // ---- barrier window: serve the refills asked for in the previous
-        // merge, one warp per row: the K smallest keys of the row over this
-        // CTA's live columns, leaving out column i (its cells were rewritten
-        // by other CTAs in this merge and may not be visible yet).  The
-        // lists are read two merges later, after the next barrier.
-        {
-            const int nexec = sh.nexec;
-            const int sbuf = (int)(t % 3);
-            for (int s = warp; s < nexec; s += (NT / 32)) {
-                const long long r = sh.exec_row[s];
-                if (r < 0 || r >= n || r == i || r == j)
-                    continue;  // the owner drops this refill
+            if (lane == 0)
+                sh.np = np;
+        } else {
+            // ---- refills served in the previous round: merge the partial
+            // lists, then replay that round's merges (the scan ran before
+            // them, or while they were being written)
+            const int ninst = sh.ninst;
+            const int ipar = par ^ 1;
+            for (int s2 = warp - 1; s2 < ninst; s2 += W - 1) {
+                const int l = sh.inst_slot[s2];
+                const int pos = pend_s[l];
+                const long long row = row_of(l);
                 u64 L[K];
 #pragma unroll
                 for (int q = 0; q < K; ++q)
                     L[q] = kNoKey;
-                const long long base = tri_off(r, n) - r - 1;  // cell (r, c) at base + c
+                for (int g = lane; g < G; g += 32) {
+                    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(
+                        p.parts + (((size_t)ipar * G + g) * kMaxReq + pos) * K);
+                    const ulonglong2 v0 = __ldcg(src), v1 = __ldcg(src + 1);
+                    list_insert(L, v0.x);
+                    list_insert(L, v0.y);
+                    list_insert(L, v1.x);
+                    list_insert(L, v1.y);
+                }
+                u64 M[K];
+                warp_topk(L, M);
+                if (lane == 0) {
+                    int c = list_count(M);
+                    u64 B = c == K ? M[K - 1] : kNoKey;
+                    const int np2 = sh.nprev;
+#pragma unroll
+                    for (int q = 0; q < K; ++q) {
+                        const int col = (int)(unsigned)M[q];
+                        for (int a = 0; a < np2; ++a) {
+                            if (M[q] != kNoKey && (col == sh.ppi[a] || col == sh.ppj[a]))
+                                M[q] = kNoKey;
+                        }
+                    }
+                    sort_list(M);
+                    c = list_count(M);
+                    const long long base = tri_off(row, n) - row - 1;  // cell (row, c) at base + c
+                    for (int a = 0; a < np2; ++a) {
+                        const long long ia = sh.ppi[a];
+                        if (ia > row) {
+                            const u64 x = make_key(__ldcg(p.D + base + ia), (unsigned)ia);
+                            if (x <= B) {
+                                list_insert(M, x);
+                                if (c == K)
+                                    B = M[K - 1];
+                                else
+                                    ++c;
+                            }
+                        }
+                    }
+                    cache_store(l, M);
+                    ccnt[l] = c;
+                    cB[l] = B;
+                    pend_t[l] = -1;
+                }
+            }
+            if (tid == 32)
+                st_installs += ninst;
+        }
+        __syncthreads();
+        const int s = sh.np;
+        {
+            // every CTA read the same records and walked them the same way, so
+            // every CTA takes this exit together
+            int bad = 0;
+            if (tid < s) {
+                const int i = sh.pi[tid], j = sh.pj[tid];
+                bad = !(i >= 0 && i < j && j < n);
+            }
+            if (__syncthreads_or(bad)) {
+                if (tid == 0)
+                    atomicCAS(p.status, 0, kErrInternal);
+                return;
+            }
+        }
+
+        // ---- the chain's sizes, member flags and the cells between members
+        if (tid < S) {
+            sh.amin[tid] = kNoKey;
+            sh.hmin[tid] = kNoKey;
+            sh.gamin[tid] = kNoKey;
+            sh.ghmin[tid] = kNoKey;
+        }
+        if (tid < s) {
+            sh.szi[tid] = __ldcg(p.size_g + sh.pi[tid]);
+            sh.szj[tid] = __ldcg(p.size_g + sh.pj[tid]);
+        }
+        if (tid < 2 * s) {
+            const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
+            if (owner_of(m) == b)
+                mflag[slot_of(m)] = 1;
+        }
+        for (int e = tid; e < 4 * s * s; e += NT) {
+            const int u = e / (2 * s), v = e % (2 * s);
+            if (u < v && (u >> 1) != (v >> 1)) {
+                const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
+                const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
+                const float d = __ldcg(p.D + pair_idx(mu, mv, n));
+                sh.Dm[u][v] = d;
+                sh.Dm[v][u] = d;
+            }
+        }
+        __syncthreads();
+        // cells (i_a, i_b) and (i_a, j_b) after merge a alone
+        for (int e = tid; e < s * s; e += NT) {
+            const int a = e / s, c = e % s;
+            if (a != c) {
+                sh.X[a][c] = lw_cell(p.linkage, sh.Dm[2 * c][2 * a], sh.Dm[2 * c][2 * a + 1], sh.ph[a],
+                                     sh.szi[a], sh.szj[a], sh.szi[c]);
+                sh.Y[a][c] = lw_cell(p.linkage, sh.Dm[2 * c + 1][2 * a], sh.Dm[2 * c + 1][2 * a + 1],
+                                     sh.ph[a], sh.szi[a], sh.szj[a], sh.szj[c]);
+            }
+        }
+        lap(ph1);
+
+        // ---- pass 1: new cells of every live k outside the chain (reads only)
+        if (s > 0) {
+            for (int l0 = 0; l0 < R; l0 += NT) {
+                const int l = l0 + tid;
+                bool ok = false;
+                long long k = 0;
+                int nk = 1;
+                if (l < R) {
+                    k = row_of(l);
+                    ok = k < n && live(bitmap, k) && !mflag[l];
+                    if (ok)
+                        nk = rsize[l];
+                }
+                float va[S], vb[S];
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    va[a] = 0.0f;
+                    vb[a] = 0.0f;
+                    if (ok && a < s) {
+                        va[a] = __ldcg(p.D + pair_idx(k, sh.pi[a], n));
+                        vb[a] = __ldcg(p.D + pair_idx(k, sh.pj[a], n));
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    if (a >= s)
+                        break;
+                    u64 ka = kNoKey, kh = kNoKey;
+                    if (ok) {
+                        const float v = lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                        ka = make_key(v, (unsigned)k);
+                        if (k > sh.pi[a])
+                            kh = ka;
+                    }
+                    const u64 ma = warp_u64_min(ka);
+                    const u64 mh = warp_u64_min(kh);
+                    if (lane == 0) {
+                        if (ma != kNoKey)
+                            atomicMin(&sh.amin[a], ma);
+                        if (mh != kNoKey)
+                            atomicMin(&sh.hmin[a], mh);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // cell (i_a, i_b) after merge a and then merge b
+        for (int e = tid; e < s * s; e += NT) {
+            const int a = e / s, c = e % s;
+            if (a < c)
+                sh.C[a][c] = lw_cell(p.linkage, sh.X[a][c], sh.Y[a][c], sh.ph[c], sh.szi[c], sh.szj[c],
+                                     sh.szi[a] + sh.szj[a]);
+        }
+        if (tid < 2 * S)
+            __stcg(p.recB + (size_t)b * 2 * S + tid, tid < S ? sh.amin[tid] : sh.hmin[tid - S]);
+        lap(ph2);
+        grid_arrive(p, epoch);
+
+        // ---- window of barrier B: serve the refills asked for in round r - 1,
+        // one warp per row: the K smallest keys of the row over this CTA's
+        // live columns.  Nobody rewrites a cell before the barrier except the
+        // cells of this round's merges, which the install replays.
+        {
+            const int nexec = sh.nexec;
+            for (int s2 = warp; s2 < nexec; s2 += W) {
+                const long long rr = sh.exec_row[s2];
+                if (rr < 0 || rr >= n - 1)
+                    continue;
+                u64 L[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q)
+                    L[q] = kNoKey;
+                const long long base = tri_off(rr, n) - rr - 1;  // cell (rr, c) at base + c
                 long long cnt = 0;
                 for (long long qb0 = 0; qb0 < my_blocks; qb0 += 16) {
                     float v[16];
@@ -1007,7 +1000,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         const long long qb = qb0 + u;
                         const long long c = ((long long)b + (long long)G * qb) * kRowBlock + lane;
                         v[u] = -1.0f;  // marks "no cell"; real cells are >= 0
-                        if (qb < my_blocks && c > r && c < n && c != i && live(bitmap, c))
+                        if (qb < my_blocks && c > rr && c < n && live(bitmap, c))
                             v[u] = __ldcg(p.D + base + c);
                     }
 #pragma unroll
@@ -1024,37 +1017,285 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 warp_topk(L, w);
                 if (lane < K / 2) {
                     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
-                        p.parts + (((size_t)sbuf * G + b) * kMaxReq + s) * K);
+                        p.parts + (((size_t)par * G + b) * kMaxReq + s2) * K);
                     __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
                 }
             }
             st_fills += nexec;
         }
+        lap(ph3);
+        if (!grid_wait(p, epoch, sh))
+            return;
+        lap(ph0);
+
+        // ---- B: the global per-pair minima, then the certified prefix
+        if (s > 0) {
+            const int a = tid % S;
+            u64 ma = kNoKey, mh = kNoKey;
+            if (a < s) {
+                for (int g = tid / S; g < G; g += NT / S) {
+                    const u64 x = __ldcg(p.recB + (size_t)g * 2 * S + a);
+                    const u64 y = __ldcg(p.recB + (size_t)g * 2 * S + S + a);
+                    ma = x < ma ? x : ma;
+                    mh = y < mh ? y : mh;
+                }
+            }
+#pragma unroll
+            for (int o = S; o < 32; o <<= 1) {
+                const u64 x = __shfl_xor_sync(kFull, ma, o);
+                const u64 y = __shfl_xor_sync(kFull, mh, o);
+                ma = x < ma ? x : ma;
+                mh = y < mh ? y : mh;
+            }
+            if (lane < S && a < s) {
+                if (ma != kNoKey)
+                    atomicMin(&sh.gamin[a], ma);
+                if (mh != kNoKey)
+                    atomicMin(&sh.ghmin[a], mh);
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane p checks P_p against every cell that merges 0..p-1 rewrote
+            bool okp = true;
+            if (lane >= 1 && lane < s) {
+                const int pp = lane;
+                Cand P;
+                P.A = ((u64)__float_as_uint(sh.ph[pp]) << 32) | (unsigned)sh.pi[pp];
+                P.c = (unsigned)sh.pj[pp];
+                Cand M = {kNoKey, 0xffffffffu};
+                for (int a = 0; a < pp; ++a) {
+                    const unsigned ia = (unsigned)sh.pi[a];
+                    const u64 g = sh.gamin[a];
+                    if (g != kNoKey)
+                        cand_min(M, cell_cand((unsigned)(g >> 32), ia, (unsigned)g));
+                    for (int c = pp; c < s; ++c) {
+                        cand_min(M, cell_cand(__float_as_uint(sh.X[a][c]), ia, (unsigned)sh.pi[c]));
+                        cand_min(M, cell_cand(__float_as_uint(sh.Y[a][c]), ia, (unsigned)sh.pj[c]));
+                    }
+                    for (int c = a + 1; c < pp; ++c)
+                        cand_min(M, cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]));
+                }
+                okp = P.A < M.A || (P.A == M.A && P.c < M.c);
+            }
+            const unsigned okm = __ballot_sync(kFull, okp);
+            if (lane == 0) {
+                const unsigned inchain = s >= 32 ? kFull : ((1u << s) - 1u);
+                const unsigned bad = ~okm & inchain & ~1u;
+                sh.nacc = bad ? __ffs(bad) - 1 : s;
+                sh.ninst = 0;
+            }
+        }
+        __syncthreads();
+        const int L = sh.nacc;
+
+        // ---- bookkeeping of the L merges
+        if (b == 0) {
+            if (tid < L) {
+                p.merges[2 * (t + tid)] = (int32_t)sh.pi[tid];
+                p.merges[2 * (t + tid) + 1] = (int32_t)sh.pj[tid];
+                p.heights[t + tid] = sh.ph[tid];
+                __stcg(p.size_g + sh.pi[tid], sh.szi[tid] + sh.szj[tid]);
+            }
+            for (int e = tid; e < L * L; e += NT) {
+                const int a = e / L, c = e % L;
+                if (a < c)
+                    __stcg(p.D + pair_idx(sh.pi[a], sh.pi[c], n), sh.C[a][c]);
+            }
+            // each pair a < c stands for three updates of the step-by-step
+            // order: merge a rewrites (i_a, i_c) and (i_a, j_c), merge c (i_c, i_a)
+            if (tid == 0)
+                st_updates += 3LL * L * (L - 1) / 2;
+        }
+        if (tid < L) {
+            const int j = sh.pj[tid];
+            atomicAnd(&bitmap[j >> 5], ~(1u << (j & 31)));  // Section 4 step 2: slot j retires
+        }
+        if (tid >= 2 * L && tid < 2 * s) {
+            const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
+            if (owner_of(m) == b)
+                mflag[slot_of(m)] = 0;  // proposed but not merged this round
+        }
+        if (tid < L) {
+            const int a = tid;
+            const long long ja = sh.pj[a];
+            if (owner_of(ja) == b) {
+                const int l = slot_of(ja);
+                ccnt[l] = 0;
+                cB[l] = kNoKey;
+                pend_t[l] = -1;
+            }
+            const long long ia = sh.pi[a];
+            if (owner_of(ia) == b) {
+                // the survivor's cache: its smallest new cell outside the chain
+                // and, below it, the new cells to chain members
+                const int l = slot_of(ia);
+                const u64 m = sh.ghmin[a];
+                u64 M[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q)
+                    M[q] = kNoKey;
+                int ncand = 0;
+                for (int c = 0; c < s; ++c) {
+                    if (c == a)
+                        continue;
+                    u64 x0 = kNoKey, x1 = kNoKey;
+                    if (c < L) {
+                        if (sh.pi[c] > ia)
+                            x0 = make_key(a < c ? sh.C[a][c] : sh.C[c][a], (unsigned)sh.pi[c]);
+                    } else {
+                        if (sh.pi[c] > ia)
+                            x0 = make_key(sh.X[a][c], (unsigned)sh.pi[c]);
+                        if (sh.pj[c] > ia)
+                            x1 = make_key(sh.Y[a][c], (unsigned)sh.pj[c]);
+                    }
+                    if (x0 != kNoKey && x0 < m) {
+                        list_insert(M, x0);
+                        ++ncand;
+                    }
+                    if (x1 != kNoKey && x1 < m) {
+                        list_insert(M, x1);
+                        ++ncand;
+                    }
+                }
+                int c;
+                u64 B;
+                if (m != kNoKey) {
+                    list_insert(M, m);
+                    c = list_count(M);
+                    B = M[c - 1];
+                } else {
+                    c = list_count(M);
+                    B = ncand > K ? M[K - 1] : kNoKey;
+                }
+                cache_store(l, M);
+                ccnt[l] = c;
+                cB[l] = B;
+                rsize[l] = sh.szi[a] + sh.szj[a];
+                pend_t[l] = -1;
+                if (c <= kRefillAt && B != kNoKey)
+                    request(l, r);
+            }
+        }
+        __syncthreads();
+        lap(ph4);
+
+        // ---- pass 2: apply the L merges to every live k outside them (in a
+        // round without merges it only renews refill requests that the
+        // per-round cap turned away: a row waiting for one may hold every
+        // later round up)
+        {
+            for (int l0 = 0; l0 < R; l0 += NT) {
+                const int l = l0 + tid;
+                bool ok = false;
+                long long k = 0;
+                int nk = 1;
+                if (l < R) {
+                    k = row_of(l);
+                    ok = k < n && live(bitmap, k) && !mflag[l];
+                    if (ok)
+                        nk = rsize[l];
+                }
+                if (!ok)
+                    continue;
+                float va[S], vb[S];
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    va[a] = 0.0f;
+                    vb[a] = 0.0f;
+                    if (a < L) {
+                        va[a] = __ldcg(p.D + pair_idx(k, sh.pi[a], n));
+                        vb[a] = __ldcg(p.D + pair_idx(k, sh.pj[a], n));
+                    }
+                }
+                u64 Cc[K];
+                cache_load(Cc, l);
+                int c = ccnt[l];
+                u64 B = cB[l];
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    if (a >= L)
+                        break;
+                    const long long ia = sh.pi[a], ja = sh.pj[a];
+                    const float v = lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                    __stcg(p.D + pair_idx(k, ia, n), v);
+                    ++st_updates;
+                    if (k < ja) {
+                        // row k loses column j; if k < i its cell (k, i) changed as well
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            const long long col = (long long)(unsigned)Cc[q];
+                            if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia)))
+                                Cc[q] = kNoKey;
+                        }
+                        close_holes(Cc);
+                        c = list_count(Cc);
+                        if (k < ia) {
+                            const u64 x = make_key(v, (unsigned)ia);
+                            if (x <= B) {
+                                list_insert(Cc, x);
+                                if (c == K)
+                                    B = Cc[K - 1];
+                                else
+                                    ++c;
+                            }
+                        }
+                    }
+                }
+                cache_store(l, Cc);
+                ccnt[l] = c;
+                cB[l] = B;
+                // (a cache that holds every live cell of its row needs no refill)
+                if (c <= kRefillAt && B != kNoKey && pend_t[l] < 0)
+                    request(l, r);
+            }
+        }
+        __syncthreads();
+        if (tid < 2 * L) {
+            const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
+            if (owner_of(m) == b)
+                mflag[slot_of(m)] = 0;
+        }
+        if (tid < L) {
+            sh.ppi[tid] = sh.pi[tid];
+            sh.ppj[tid] = sh.pj[tid];
+        }
+        if (tid == 0) {
+            sh.nprev = L;
+            ++st_rounds;
+            st_idle += L == 0;
+        }
+        t += L;
+        if (t >= n - 1)
+            break;  // that was the last merge
+        publish(r + 1);
         lap(ph5);
+        grid_arrive(p, epoch);
         if (!grid_wait(p, epoch, sh))
             return;
         lap(ph0);
     }
 
     if (p.stats) {
-        u64 *S = reinterpret_cast<u64 *>(p.stats);
-        atomicAdd(S + 1, (u64)st_resc_cells);
-        atomicAdd(S + 2, (u64)st_updates);
-        atomicAdd(S + 5, (u64)st_fill_cells);
+        u64 *St = reinterpret_cast<u64 *>(p.stats);
+        atomicAdd(St + 2, (u64)st_updates);
+        atomicAdd(St + 5, (u64)st_fill_cells);
+        if (tid == 32)
+            atomicAdd(St + 6, (u64)st_installs);
         if (tid == 0) {
-            atomicAdd(S + 0, (u64)st_rescans);
-            atomicAdd(S + 6, (u64)st_installs);
             if (b == 0) {
-                S[3] = (u64)G;
-                S[4] = (u64)st_fills;
+                St[0] = (u64)st_rounds;
+                St[1] = (u64)st_idle;
+                St[3] = (u64)G;
+                St[4] = (u64)st_fills;
             }
             if (p.timing) {
-                atomicAdd(S + 8, ph0);
-                atomicAdd(S + 9, ph1);
-                atomicAdd(S + 10, ph2);
-                atomicAdd(S + 11, ph3);
-                atomicAdd(S + 12, ph4);
-                atomicAdd(S + 13, ph5);
+                atomicAdd(St + 8, ph0);
+                atomicAdd(St + 9, ph1);
+                atomicAdd(St + 10, ph2);
+                atomicAdd(St + 11, ph3);
+                atomicAdd(St + 12, ph4);
+                atomicAdd(St + 13, ph5);
             }
         }
     }
@@ -1097,12 +1338,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
         p.aligned16 = ((uintptr_t)J.D & 15u) == 0;
         p.merges = J.merges;
         p.heights = J.heights;
-        p.size_g = reinterpret_cast<int *>(ws + L.size);
-        p.cand = reinterpret_cast<Rec *>(ws + L.cand);
-        p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
-        p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
-        p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
-        p.status = reinterpret_cast<int *>(ws + L.status);
+        bind_workspace(p, ws, L);
         p.stats = nullptr;
         p.timeout_ns = bp.timeout_ns;
         p.skip_arrive_cta = -1;
@@ -1130,7 +1366,10 @@ size_t merge_smem_bytes(long long n, int G)
     const long long nb = (n + kRowBlock - 1) / kRowBlock;
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + Rmax * (8 * K + 8 + 16 + 4 * 5));
+    // bitmap; published entries (keys, column words, walk positions); per
+    // slot: K keys, bound, size, count, refill round and position, chain flag
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * K * 12 + (((long long)G * 4 + 15) & ~15LL) +
+                    Rmax * (8 * K + 8 + 4 * 4 + 1));
 }
 
 namespace {

@@ -23,10 +23,10 @@
 namespace {
 
 // Largest n this entry point accepts and the scratch that serves it: cluster
-// sizes 4n, per-CTA candidate and partial-list records (about 3.2 KB per CTA
-// of a full-device grid), request, barrier, status and stats words.
+// sizes 4n, per-CTA records and refill lists (about 8.5 KB per CTA of a
+// full-device grid), barrier, status and stats words.
 constexpr long long kNoAllocMaxN = LW_NOALLOC_MAX_N;
-constexpr size_t kScratchBytes = 1024 * 1024;
+constexpr size_t kScratchBytes = 2 * 1024 * 1024;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -108,12 +108,7 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
     p.aligned16 = ((uintptr_t)dist & 15u) == 0;
     p.merges = merges_out;
     p.heights = heights_out;
-    p.size_g = reinterpret_cast<int *>(ws + L.size);
-    p.cand = reinterpret_cast<lw::Rec *>(ws + L.cand);
-    p.islice = reinterpret_cast<unsigned long long *>(ws + L.islice);
-    p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
-    p.bar = reinterpret_cast<unsigned *>(ws + L.bar);
-    p.status = reinterpret_cast<int *>(ws + L.status);
+    lw::bind_workspace(p, ws, L);
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = 5000ull * 1000000ull;
     p.skip_arrive_cta = -1;

@@ -181,11 +181,11 @@ def lw_get_stats(ctx: int) -> dict:
     s = lib.lw_get_stats(ctx, a, 16)
     if s != 0:
         raise LwError(s, "lw_get_stats")
-    out = {"rescans": a[0], "rescan_cells": a[1], "updated": a[2], "grid": a[3],
+    out = {"rounds": a[0], "idle_rounds": a[1], "updated": a[2], "grid": a[3],
            "refills": a[4], "refill_cells": a[5], "installs": a[6]}
     if any(a[8:14]):
         G = max(1, a[3])
-        names = ("barrier", "exchange", "installs", "update", "publish", "refill")
+        names = ("barrier", "walk", "pass1", "refill", "certify", "pass2")
         out["phase_ms"] = {nm: a[8 + q] / G / 1e6 for q, nm in enumerate(names)}
     return out
 

@@ -120,10 +120,10 @@ def test_batched_workload_sample(ctx):
 
 
 def test_batch_many_copies_of_a_rescan_heavy_job(ctx):
-    """96 copies of one tie-heavy job (frequent synchronous row rescans) in one
-    batch: every copy must equal the oracle.  Guards the ordering between a
-    rescan's cache write and the candidate scan that follows it (a missing
-    barrier there once dropped a row from the minimum search now and then)."""
+    """96 copies of one tie-heavy job (many equal cells, frequent refills) in
+    one batch: every copy must equal the oracle, every time (a missing
+    barrier between a cache write and the scan that reads it shows up as a
+    rare wrong merge in such runs)."""
     n, link = 433, 1
     D = synth.tie_heavy(n, 60, 6)
     wm, wh, _, _ = oracle.cached(D, n, link)

@@ -109,10 +109,9 @@ def test_mid_sizes_full_grid(ctx, link):
         _assert_same(_gpu(ctx, D, n, link, grid=torch.cuda.get_device_properties(0).multi_processor_count),
                      want, f"n={n}")
         st = ctx.stats()
-        # the cells rewritten are fixed by n; the row scans depend on the cache
-        # design (the oracle keeps one key per row, the kernel four)
+        # the cells rewritten are fixed by n; rounds certify one merge or more
         assert st["updated"] == want[2]["updated"]
-        assert st["rescans"] <= want[2]["rescans"]
+        assert 1 <= st["rounds"] - st["idle_rounds"] <= n - 1
 
 
 @pytest.mark.parametrize("link", [0, 1, 2])
