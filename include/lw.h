@@ -128,11 +128,14 @@ lw_status lw_wait(lw_ctx *ctx);
  *   [4] row refills served by all CTAs together,
  *   [5] live cells read by those refills,
  *   [6] refills installed by the rows' owners,
+ *   [7] published entries the walks visited (all rounds),
  *   [8..13] with LW_OPT_PHASE_TIMES on: wall-clock nanoseconds summed over
  *       the CTAs of the grid, per phase of a round: [8] barrier waits,
  *       [9] exchange, walk and refill installs, [10] pass 1 (new cells, read
  *       only), [11] refill service in the barrier window, [12] certification
- *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish.
+ *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish;
+ *   [14] rows rescanned at once by their owner (cache emptied),
+ *   [15] live cells read by those rescans.
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 

@@ -199,7 +199,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr u64 kHi = 0xffffffff00000000ull;
 static_assert(kPub == K, "a CTA publishes its entries with the K-list reductions");
 static_assert(K == 4, "sort_list is a 4-input network");
-static_assert(S <= 32 && (32 % S) == 0, "pair minima are reduced across lanes in groups of S");
+static_assert(S == 16, "certification and pair minima use groups of 16 lanes");
 
 // Sort a K-list in which any entries were replaced by kNoKey.
 __device__ __forceinline__ void sort_list(u64 (&L)[K])
@@ -264,9 +264,12 @@ struct Shared {
     int inst_slot[kReqPerCta];
     // the round's chain of proposed merges and the cells between its members
     int np, nacc;
+    unsigned front;              // value bits where this round's walk stopped
+    int okp[S];
     int pi[S], pj[S];
     float ph[S];
     int szi[S], szj[S];
+    long long bi[S], bj[S];      // row bases of the members: cell (x, c) at b + c
     u64 amin[S], hmin[S];        // this CTA's smallest new cell per pair (all k, k > i)
     u64 gamin[S], ghmin[S];      // the same over all CTAs
     float Dm[2 * S][2 * S];      // D between members (2a = i_a, 2a + 1 = j_a)
@@ -276,6 +279,7 @@ struct Shared {
     // the previous round's merges, replayed on installed refills
     int ppi[S], ppj[S];
     int nprev;
+    int nresc;                   // rows to rescan at once this round
 };
 
 // After barrier A: the list of rows to refill in this round -- every CTA's
@@ -468,6 +472,44 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
     warp_topk(L, out);
 }
 
+// K smallest keys of row r over live columns, computed by the whole CTA
+// (for a row whose cache empties before a refill arrives).  Adds the live
+// cells read to `live_cells`.  Result in sh.tko.
+template <int NT>
+__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT> &sh,
+                               long long &live_cells)
+{
+    const long long n = p.n;
+    const long long start = tri_off(r, n);
+    const long long end = start + (n - r - 1);
+    const long long base_c = r + 1 - start;
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
+    long long cnt = 0;
+    // eight loads in flight per thread
+    for (long long q0 = start + threadIdx.x; q0 < end; q0 += 8 * NT) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long q = q0 + (long long)u * NT;
+            v[u] = q < end ? __ldcg(p.D + q) : -1.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long c = q0 + (long long)u * NT + base_c;
+            if (v[u] >= 0.0f && live(bitmap, c)) {
+                ++cnt;
+                if (__float_as_uint(v[u]) <= (unsigned)(L[K - 1] >> 32))
+                    list_insert(L, make_key(v[u], (unsigned)c));
+            }
+        }
+    }
+    live_cells += cnt;
+    block_topk(L, sh);
+}
+
 // All n - 1 merges of one job, run by CTA b of the job's G CTAs (every CTA
 // of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
 // bytes of dynamic shared memory.
@@ -507,7 +549,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
     int *pend_s = pend_t + Rmax;
-    unsigned char *mflag = reinterpret_cast<unsigned char *>(pend_s + Rmax);
+    int *rlist = pend_s + Rmax;
+    unsigned char *mflag = reinterpret_cast<unsigned char *>(rlist + Rmax);
 
     auto row_of = [&](int l) -> long long {
         return (long long)((long long)b + (long long)G * (l >> 5)) * kRowBlock + (l & 31);
@@ -547,8 +590,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
     };
 
-    long long st_updates = 0, st_fill_cells = 0;
-    long long st_fills = 0, st_installs = 0, st_rounds = 0, st_idle = 0;
+    long long st_updates = 0, st_fill_cells = 0, st_rescans = 0, st_resc_cells = 0;
+    long long st_fills = 0, st_installs = 0, st_rounds = 0, st_idle = 0, st_walk = 0;
 
     // The records of round rr: this CTA's kPub smallest entries (cached keys
     // and bound marks of its rows) and its refill requests of round rr - 1.
@@ -563,13 +606,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             const u64 B = cB[l];
             if (c > 0 || B != kNoKey) {
                 const u64 rowbits = (u64)row_of(l) << 3;
+                // a row's entries ascend: stop at the first one that cannot enter
 #pragma unroll
                 for (int q = 0; q < K; ++q) {
-                    if (q < c)
-                        list_insert(Lst, (ck[(size_t)q * Rmax + l] & kHi) | rowbits | (u64)q);
+                    if (q < c) {
+                        const u64 e = (ck[(size_t)q * Rmax + l] & kHi) | rowbits | (u64)q;
+                        if (e < Lst[K - 1])
+                            list_insert(Lst, e);
+                    }
                 }
-                if (B != kNoKey)
-                    list_insert(Lst, (B & kHi) | rowbits | (u64)c);
+                if (B != kNoKey) {
+                    const u64 e = (B & kHi) | rowbits | (u64)c;
+                    if (e < Lst[K - 1])
+                        list_insert(Lst, e);
+                }
             }
             if (rr >= 2 && pend_t[l] == rr - 2) {
                 const int s2 = atomicAdd(&sh.ninst, 1);
@@ -632,6 +682,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         sh.nmyreq[0] = 0;
         sh.nmyreq[1] = 0;
         sh.nprev = 0;
+        sh.nresc = 0;
     }
 
     // ---- phase 0: validate the matrix and fill the caches of owned rows
@@ -749,10 +800,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
             int np = 0;
             int member = -1;  // lane 2a holds i_a, lane 2a + 1 holds j_a
+            unsigned front = 0;  // value bits of the last entry visited
             for (int guard = 0; guard <= G * K; ++guard) {
                 const u64 m = warp_u64_min(lm);
                 if (m == kNoKey)
                     break;
+                ++st_walk;
+                front = (unsigned)(m >> 32);
                 const int src = __ffs(__ballot_sync(kFull, lm == m)) - 1;
                 unsigned col = 0;
                 if (lane == src) {
@@ -799,8 +853,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (stop)
                     break;
             }
-            if (lane == 0)
+            if (lane == 0) {
                 sh.np = np;
+                sh.front = front;
+            }
         } else {
             // ---- refills served in the previous round: merge the partial
             // lists, then replay that round's merges (the scan ran before
@@ -826,10 +882,22 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
                 u64 M[K];
                 warp_topk(L, M);
+                // the new cells (row, i_a) of the previous round's merges, one lane each
+                const int np2 = sh.nprev;
+                const long long base = tri_off(row, n) - row - 1;  // cell (row, c) at base + c
+                u64 xr = kNoKey;
+                if (lane < np2) {
+                    const long long ia = sh.ppi[lane];
+                    if (ia > row)
+                        xr = make_key(__ldcg(p.D + base + ia), (unsigned)ia);
+                }
+                u64 xs[S];
+#pragma unroll
+                for (int a = 0; a < S; ++a)
+                    xs[a] = __shfl_sync(kFull, xr, a);
                 if (lane == 0) {
                     int c = list_count(M);
                     u64 B = c == K ? M[K - 1] : kNoKey;
-                    const int np2 = sh.nprev;
 #pragma unroll
                     for (int q = 0; q < K; ++q) {
                         const int col = (int)(unsigned)M[q];
@@ -840,18 +908,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     }
                     sort_list(M);
                     c = list_count(M);
-                    const long long base = tri_off(row, n) - row - 1;  // cell (row, c) at base + c
-                    for (int a = 0; a < np2; ++a) {
-                        const long long ia = sh.ppi[a];
-                        if (ia > row) {
-                            const u64 x = make_key(__ldcg(p.D + base + ia), (unsigned)ia);
-                            if (x <= B) {
-                                list_insert(M, x);
-                                if (c == K)
-                                    B = M[K - 1];
-                                else
-                                    ++c;
-                            }
+#pragma unroll
+                    for (int a = 0; a < S; ++a) {
+                        const u64 x = xs[a];
+                        if (x != kNoKey && x <= B) {
+                            list_insert(M, x);
+                            if (c == K)
+                                B = M[K - 1];
+                            else
+                                ++c;
                         }
                     }
                     cache_store(l, M);
@@ -890,6 +955,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         if (tid < s) {
             sh.szi[tid] = __ldcg(p.size_g + sh.pi[tid]);
             sh.szj[tid] = __ldcg(p.size_g + sh.pj[tid]);
+            const long long i = sh.pi[tid], j = sh.pj[tid];
+            sh.bi[tid] = tri_off(i, n) - i - 1;  // cell (i, c) at bi + c for c > i
+            sh.bj[tid] = tri_off(j, n) - j - 1;
         }
         if (tid < 2 * s) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
@@ -919,7 +987,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         lap(ph1);
 
-        // ---- pass 1: new cells of every live k outside the chain (reads only)
+        // ---- pass 1: new cells of every live k outside the chain (reads only);
+        // the values of each thread's first row stay in registers for pass 2
+        float kv[S];
+        bool kok = false;
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+            kv[a] = 0.0f;
         if (s > 0) {
             for (int l0 = 0; l0 < R; l0 += NT) {
                 const int l = l0 + tid;
@@ -933,13 +1007,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         nk = rsize[l];
                 }
                 float va[S], vb[S];
+                const long long bk = tri_off(k, n) - k - 1;  // cell (k, c) at bk + c for c > k
 #pragma unroll
                 for (int a = 0; a < S; ++a) {
                     va[a] = 0.0f;
                     vb[a] = 0.0f;
                     if (ok && a < s) {
-                        va[a] = __ldcg(p.D + pair_idx(k, sh.pi[a], n));
-                        vb[a] = __ldcg(p.D + pair_idx(k, sh.pj[a], n));
+                        const long long i = sh.pi[a], j = sh.pj[a];
+                        va[a] = __ldcg(p.D + (k < i ? bk + i : sh.bi[a] + k));
+                        vb[a] = __ldcg(p.D + (k < j ? bk + j : sh.bj[a] + k));
                     }
                 }
 #pragma unroll
@@ -949,6 +1025,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     u64 ka = kNoKey, kh = kNoKey;
                     if (ok) {
                         const float v = lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                        if (l0 == 0)
+                            kv[a] = v;
                         ka = make_key(v, (unsigned)k);
                         if (k > sh.pi[a])
                             kh = ka;
@@ -962,6 +1040,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                             atomicMin(&sh.hmin[a], mh);
                     }
                 }
+                if (l0 == 0)
+                    kok = ok;
             }
         }
         __syncthreads();
@@ -978,47 +1058,79 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         grid_arrive(p, epoch);
 
         // ---- window of barrier B: serve the refills asked for in round r - 1,
-        // one warp per row: the K smallest keys of the row over this CTA's
-        // live columns.  Nobody rewrites a cell before the barrier except the
-        // cells of this round's merges, which the install replays.
+        // two rows per warp at a time: the K smallest keys of each row over
+        // this CTA's live columns.  Nobody rewrites a cell before the barrier
+        // except the cells of this round's merges, which the install replays.
         {
             const int nexec = sh.nexec;
-            for (int s2 = warp; s2 < nexec; s2 += W) {
-                const long long rr = sh.exec_row[s2];
-                if (rr < 0 || rr >= n - 1)
-                    continue;
-                u64 L[K];
+            // first block of this CTA holding a column > rr
+            auto first_block = [&](long long rr) -> long long {
+                const long long blk = (rr + 1) / kRowBlock;
+                return blk <= b ? 0 : (blk - b + G - 1) / G;
+            };
+            for (int s0 = warp; s0 < nexec; s0 += 2 * W) {
+                const int s1 = s0 + W;
+                long long ra = sh.exec_row[s0];
+                long long rb = s1 < nexec ? sh.exec_row[s1] : -1;
+                if (ra < 0 || ra >= n - 1)
+                    ra = -1;
+                if (rb < 0 || rb >= n - 1)
+                    rb = -1;
+                const long long qa = ra >= 0 ? first_block(ra) : my_blocks;
+                const long long qbb = rb >= 0 ? first_block(rb) : my_blocks;
+                const float *Da = p.D + (ra >= 0 ? tri_off(ra, n) - ra - 1 : 0);  // cell (ra, c) at Da[c]
+                const float *Db = p.D + (rb >= 0 ? tri_off(rb, n) - rb - 1 : 0);
+                u64 La[K], Lb[K];
 #pragma unroll
-                for (int q = 0; q < K; ++q)
-                    L[q] = kNoKey;
-                const long long base = tri_off(rr, n) - rr - 1;  // cell (rr, c) at base + c
+                for (int q = 0; q < K; ++q) {
+                    La[q] = kNoKey;
+                    Lb[q] = kNoKey;
+                }
                 long long cnt = 0;
-                for (long long qb0 = 0; qb0 < my_blocks; qb0 += 16) {
-                    float v[16];
+                for (long long q0 = qa < qbb ? qa : qbb; q0 < my_blocks; q0 += 8) {
+                    float va[8], vb[8];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const long long qb = qb0 + u;
-                        const long long c = ((long long)b + (long long)G * qb) * kRowBlock + lane;
-                        v[u] = -1.0f;  // marks "no cell"; real cells are >= 0
-                        if (qb < my_blocks && c > rr && c < n && live(bitmap, c))
-                            v[u] = __ldcg(p.D + base + c);
+                    for (int u = 0; u < 8; ++u) {
+                        const long long qq = q0 + u;
+                        const long long c = ((long long)b + (long long)G * qq) * kRowBlock + lane;
+                        const bool in = qq < my_blocks && c < n;
+                        va[u] = (in && qq >= qa && c > ra) ? __ldcg(Da + c) : -1.0f;
+                        vb[u] = (in && qq >= qbb && c > rb) ? __ldcg(Db + c) : -1.0f;
                     }
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        if (v[u] >= 0.0f) {
-                            const long long c = ((long long)b + (long long)G * (qb0 + u)) * kRowBlock + lane;
-                            list_insert(L, make_key(v[u], (unsigned)c));
-                            ++cnt;
+                    for (int u = 0; u < 8; ++u) {
+                        // dead columns were read too (their cells are stale, not
+                        // out of bounds) and are dropped here
+                        const unsigned c = (unsigned)(((long long)b + (long long)G * (q0 + u)) * kRowBlock + lane);
+                        if ((va[u] >= 0.0f || vb[u] >= 0.0f) && live(bitmap, c)) {
+                            if (va[u] >= 0.0f) {
+                                ++cnt;
+                                if (__float_as_uint(va[u]) <= (unsigned)(La[K - 1] >> 32))
+                                    list_insert(La, make_key(va[u], c));
+                            }
+                            if (vb[u] >= 0.0f) {
+                                ++cnt;
+                                if (__float_as_uint(vb[u]) <= (unsigned)(Lb[K - 1] >> 32))
+                                    list_insert(Lb, make_key(vb[u], c));
+                            }
                         }
                     }
                 }
                 st_fill_cells += cnt;
                 u64 w[K];
-                warp_topk(L, w);
-                if (lane < K / 2) {
+                warp_topk(La, w);
+                if (lane < K / 2 && ra >= 0) {
                     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
-                        p.parts + (((size_t)par * G + b) * kMaxReq + s2) * K);
+                        p.parts + (((size_t)par * G + b) * kMaxReq + s0) * K);
                     __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
+                }
+                if (s1 < nexec) {
+                    warp_topk(Lb, w);
+                    if (lane < K / 2 && rb >= 0) {
+                        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
+                            p.parts + (((size_t)par * G + b) * kMaxReq + s1) * K);
+                        __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
+                    }
                 }
             }
             st_fills += nexec;
@@ -1055,36 +1167,48 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            // lane p checks P_p against every cell that merges 0..p-1 rewrote
-            bool okp = true;
-            if (lane >= 1 && lane < s) {
-                const int pp = lane;
-                Cand P;
-                P.A = ((u64)__float_as_uint(sh.ph[pp]) << 32) | (unsigned)sh.pi[pp];
-                P.c = (unsigned)sh.pj[pp];
-                Cand M = {kNoKey, 0xffffffffu};
-                for (int a = 0; a < pp; ++a) {
-                    const unsigned ia = (unsigned)sh.pi[a];
-                    const u64 g = sh.gamin[a];
-                    if (g != kNoKey)
-                        cand_min(M, cell_cand((unsigned)(g >> 32), ia, (unsigned)g));
-                    for (int c = pp; c < s; ++c) {
-                        cand_min(M, cell_cand(__float_as_uint(sh.X[a][c]), ia, (unsigned)sh.pi[c]));
-                        cand_min(M, cell_cand(__float_as_uint(sh.Y[a][c]), ia, (unsigned)sh.pj[c]));
-                    }
-                    for (int c = a + 1; c < pp; ++c)
-                        cand_min(M, cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]));
+        // certification: thread (p, a) takes the smallest cell that merge a
+        // (a < p) rewrote as seen after merge p - 1; the 16 threads of p reduce
+        // and compare with P_p
+        for (int e = tid; e < 16 * S; e += NT) {
+            const int pp = e >> 4, a = e & 15;
+            Cand M = {kNoKey, 0xffffffffu};
+            if (pp >= 1 && pp < s && a < pp) {
+                const unsigned ia = (unsigned)sh.pi[a];
+                const u64 g = sh.gamin[a];
+                if (g != kNoKey)
+                    cand_min(M, cell_cand((unsigned)(g >> 32), ia, (unsigned)g));
+                for (int c = pp; c < s; ++c) {
+                    cand_min(M, cell_cand(__float_as_uint(sh.X[a][c]), ia, (unsigned)sh.pi[c]));
+                    cand_min(M, cell_cand(__float_as_uint(sh.Y[a][c]), ia, (unsigned)sh.pj[c]));
                 }
-                okp = P.A < M.A || (P.A == M.A && P.c < M.c);
+                for (int c = a + 1; c < pp; ++c)
+                    cand_min(M, cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]));
             }
-            const unsigned okm = __ballot_sync(kFull, okp);
-            if (lane == 0) {
-                const unsigned inchain = s >= 32 ? kFull : ((1u << s) - 1u);
-                const unsigned bad = ~okm & inchain & ~1u;
-                sh.nacc = bad ? __ffs(bad) - 1 : s;
-                sh.ninst = 0;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                Cand y;
+                y.A = __shfl_xor_sync(kFull, M.A, o);
+                y.c = __shfl_xor_sync(kFull, M.c, o);
+                cand_min(M, y);
             }
+            if (a == 0 && pp >= 1 && pp < s) {
+                const u64 PA = ((u64)__float_as_uint(sh.ph[pp]) << 32) | (unsigned)sh.pi[pp];
+                const unsigned Pc = (unsigned)sh.pj[pp];
+                sh.okp[pp] = PA < M.A || (PA == M.A && Pc < M.c);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int L = s;
+            for (int pp = 1; pp < s; ++pp) {
+                if (!sh.okp[pp]) {
+                    L = pp;
+                    break;
+                }
+            }
+            sh.nacc = L;
+            sh.ninst = 0;
         }
         __syncthreads();
         const int L = sh.nacc;
@@ -1198,14 +1322,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
                 if (!ok)
                     continue;
+                // rows outside the chain kept their pass-1 values; rows of
+                // pairs the round did not merge, and rows past a thread's
+                // first, compute them now
+                const bool have = l0 == 0 && kok;
+                const long long bk = tri_off(k, n) - k - 1;  // cell (k, c) at bk + c for c > k
                 float va[S], vb[S];
 #pragma unroll
                 for (int a = 0; a < S; ++a) {
                     va[a] = 0.0f;
                     vb[a] = 0.0f;
-                    if (a < L) {
-                        va[a] = __ldcg(p.D + pair_idx(k, sh.pi[a], n));
-                        vb[a] = __ldcg(p.D + pair_idx(k, sh.pj[a], n));
+                    if (!have && a < L) {
+                        const long long i = sh.pi[a], j = sh.pj[a];
+                        va[a] = __ldcg(p.D + (k < i ? bk + i : sh.bi[a] + k));
+                        vb[a] = __ldcg(p.D + (k < j ? bk + j : sh.bj[a] + k));
                     }
                 }
                 u64 Cc[K];
@@ -1217,19 +1347,25 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     if (a >= L)
                         break;
                     const long long ia = sh.pi[a], ja = sh.pj[a];
-                    const float v = lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                    __stcg(p.D + pair_idx(k, ia, n), v);
+                    const float v =
+                        have ? kv[a] : lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                    __stcg(p.D + (k < ia ? bk + ia : sh.bi[a] + k), v);
                     ++st_updates;
                     if (k < ja) {
                         // row k loses column j; if k < i its cell (k, i) changed as well
+                        bool drop = false;
 #pragma unroll
                         for (int q = 0; q < K; ++q) {
                             const long long col = (long long)(unsigned)Cc[q];
-                            if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia)))
+                            if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia))) {
                                 Cc[q] = kNoKey;
+                                drop = true;
+                            }
                         }
-                        close_holes(Cc);
-                        c = list_count(Cc);
+                        if (drop) {
+                            close_holes(Cc);
+                            c = list_count(Cc);
+                        }
                         if (k < ia) {
                             const u64 x = make_key(v, (unsigned)ia);
                             if (x <= B) {
@@ -1245,12 +1381,36 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 cache_store(l, Cc);
                 ccnt[l] = c;
                 cB[l] = B;
-                // (a cache that holds every live cell of its row needs no refill)
-                if (c <= kRefillAt && B != kNoKey && pend_t[l] < 0)
+                if (c == 0 && B != kNoKey && (unsigned)(B >> 32) <= sh.front) {
+                    // live cells remain, none is cached, and the bound sits at
+                    // the front of the merges: its bare stop mark would hold
+                    // the next rounds up until a refill lands, so rescan now
+                    rlist[atomicAdd(&sh.nresc, 1)] = l;
+                    pend_t[l] = -1;
+                } else if (c <= kRefillAt && B != kNoKey && pend_t[l] < 0) {
+                    // (a cache that holds every live cell of its row needs no refill)
                     request(l, r);
+                }
             }
         }
         __syncthreads();
+        // ---- rows whose cache emptied
+        {
+            const int nresc = sh.nresc;
+            for (int q = 0; q < nresc; ++q) {
+                const int l = rlist[q];
+                block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
+                if (tid == 0) {
+                    cache_store(l, sh.tko);
+                    const int c = list_count(sh.tko);
+                    ccnt[l] = c;
+                    cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
+                }
+            }
+            st_rescans += nresc;
+            if (nresc > 0)
+                __syncthreads();  // the rescanned caches (written by thread 0) before anyone reads them
+        }
         if (tid < 2 * L) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
             if (owner_of(m) == b)
@@ -1262,6 +1422,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         if (tid == 0) {
             sh.nprev = L;
+            sh.nresc = 0;
             ++st_rounds;
             st_idle += L == 0;
         }
@@ -1280,12 +1441,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         u64 *St = reinterpret_cast<u64 *>(p.stats);
         atomicAdd(St + 2, (u64)st_updates);
         atomicAdd(St + 5, (u64)st_fill_cells);
+        atomicAdd(St + 15, (u64)st_resc_cells);
         if (tid == 32)
             atomicAdd(St + 6, (u64)st_installs);
+        if (tid == 0)
+            atomicAdd(St + 14, (u64)st_rescans);
         if (tid == 0) {
             if (b == 0) {
                 St[0] = (u64)st_rounds;
                 St[1] = (u64)st_idle;
+                St[7] = (u64)st_walk;
                 St[3] = (u64)G;
                 St[4] = (u64)st_fills;
             }
@@ -1369,7 +1534,7 @@ size_t merge_smem_bytes(long long n, int G)
     // bitmap; published entries (keys, column words, walk positions); per
     // slot: K keys, bound, size, count, refill round and position, chain flag
     return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * K * 12 + (((long long)G * 4 + 15) & ~15LL) +
-                    Rmax * (8 * K + 8 + 4 * 4 + 1));
+                    Rmax * (8 * K + 8 + 4 * 5 + 1));
 }
 
 namespace {

@@ -182,7 +182,8 @@ def lw_get_stats(ctx: int) -> dict:
     if s != 0:
         raise LwError(s, "lw_get_stats")
     out = {"rounds": a[0], "idle_rounds": a[1], "updated": a[2], "grid": a[3],
-           "refills": a[4], "refill_cells": a[5], "installs": a[6]}
+           "refills": a[4], "refill_cells": a[5], "installs": a[6], "walk_steps": a[7],
+           "rescans": a[14], "rescan_cells": a[15]}
     if any(a[8:14]):
         G = max(1, a[3])
         names = ("barrier", "walk", "pass1", "refill", "certify", "pass2")
