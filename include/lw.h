@@ -84,9 +84,10 @@ lw_status lw_create(lw_ctx **out, int device, void *cuda_stream);
 /*
  * lw_cluster -- cluster one matrix; blocks until the outputs are written.
  *   dist         packed upper triangle, n(n-1)/2 FP32 cells, row-major.
- *                If it is a DEVICE pointer it is the working matrix and is
- *                OVERWRITTEN in place (the paper's update rewrites row and
- *                column i in place, Section 5.3 step 6): keep a copy if needed.
+ *                If it is a DEVICE pointer it may be used as the working
+ *                matrix and OVERWRITTEN in place (the paper's update rewrites
+ *                row and column i in place, Section 5.3 step 6): keep a copy
+ *                if needed.
  *                If it is a HOST pointer the library copies it to a device
  *                buffer owned by the context and leaves the host array
  *                unchanged (pinned memory gives the fastest copy).
@@ -156,7 +157,12 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *                     jobs of a batch run over the whole device;
  *   LW_OPT_CTA_THREADS  threads per CTA of lw_cluster's kernel: 128, 256 or
  *                     512 (0: 512).  Smaller CTAs suit small matrices run
- *                     side by side (several fit one SM).
+ *                     side by side (several fit one SM);
+ *   LW_OPT_LAYOUT     working matrix of lw_cluster: 0 or 2 the packed
+ *                     triangle (dist itself), 1 a symmetric n x n copy
+ *                     (4n^2 bytes held by the context, used when it fits in
+ *                     half the free device memory, else the triangle).
+ *                     Results are the same either way.
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
 enum {
@@ -165,7 +171,8 @@ enum {
     LW_OPT_TEST_SKIP_ARRIVE = 3,
     LW_OPT_PHASE_TIMES = 4,
     LW_OPT_BATCH_SPLIT = 5,
-    LW_OPT_CTA_THREADS = 6
+    LW_OPT_CTA_THREADS = 6,
+    LW_OPT_LAYOUT = 7
 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 

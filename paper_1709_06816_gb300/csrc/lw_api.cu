@@ -22,6 +22,7 @@ struct lw_ctx {
     int num_sms = 0;
     int grid_opt = 0;
     int cta_threads = lw::kThreads;  // CTA size of the merge kernel (128, 256, 512)
+    int layout_opt = 0;              // 0 automatic, 1 full symmetric matrix, 2 packed triangle
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
     int phase_timing = 0;
@@ -33,6 +34,8 @@ struct lw_ctx {
     size_t ws_cap = 0;
     float *dbuf = nullptr;  // device copy of a host matrix
     size_t dbuf_cap = 0;
+    void *full = nullptr;   // symmetric n x n working matrix (multi-CTA runs)
+    size_t full_cap = 0;
     void *obuf = nullptr;   // device outputs for host output pointers
     size_t obuf_cap = 0;
     int *h_status = nullptr;       // pinned [4]
@@ -151,12 +154,37 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     if (s != LW_OK)
         return s;
     char *ws = static_cast<char *>(ctx->ws);
+
+    // On request the kernel works on a symmetric n x n copy: each merge then
+    // reads rows i and j as consecutive words instead of one scattered cell
+    // per row of the packed triangle, but must write the new column as well
+    // (one scattered word per row).  On GB300 the two cost about the same, so
+    // the packed triangle, which needs no extra memory, is the default.
+    bool use_full = false;
+    const size_t full_bytes = (size_t)n * (size_t)n * sizeof(float);
+    if (ctx->layout_opt == 1) {
+        size_t free_b = 0, total_b = 0;
+        if (ctx->full_cap >= full_bytes) {
+            use_full = true;
+        } else if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+                   full_bytes + ctx->full_cap <= free_b / 2 && (n + 31) / 32 <= 65535) {
+            use_full = true;
+        }
+        cudaGetLastError();
+        if (use_full) {
+            s = ensure(ctx, &ctx->full, &ctx->full_cap, full_bytes, "full matrix");
+            if (s != LW_OK)
+                return s;
+        }
+    }
+
     lw::MergeParams p;
-    p.D = ddist;
+    p.D = use_full ? static_cast<float *>(ctx->full) : ddist;
+    p.full = use_full ? 1 : 0;
     p.n = n;
     p.linkage = linkage;
     p.G = G;
-    p.aligned16 = ((uintptr_t)ddist & 15u) == 0;
+    p.aligned16 = ((uintptr_t)p.D & 15u) == 0;
     p.merges = dmerges;
     p.heights = dheights;
     lw::bind_workspace(p, ws, L);
@@ -172,6 +200,8 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     // barrier, status and stats words are contiguous
     if ((e = cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
+    if (use_full && (e = lw::launch_expand(ddist, p.D, n, p.status, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "expand kernel launch");
     if ((e = lw::launch_merge(p, ctx->cta_threads, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaLaunchCooperativeKernel");
     return LW_OK;
@@ -411,6 +441,11 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
         return LW_OK;
     case LW_OPT_PHASE_TIMES:
         ctx->phase_timing = value != 0;
+        return LW_OK;
+    case LW_OPT_LAYOUT:
+        if (value < 0 || value > 2)
+            return LW_ERR_INVALID_ARG;
+        ctx->layout_opt = (int)value;
         return LW_OK;
     case LW_OPT_CTA_THREADS:
         if (value != 0 && value != 128 && value != 256 && value != 512)
@@ -801,6 +836,7 @@ void lw_destroy(lw_ctx *ctx)
         cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws);
     cudaFree(ctx->dbuf);
+    cudaFree(ctx->full);
     cudaFree(ctx->obuf);
     cudaFreeHost(ctx->h_status);
     cudaFreeHost(ctx->h_stats);

@@ -38,7 +38,10 @@ struct __align__(16) RecA {
 };
 
 struct MergeParams {
-    float *D;                      // packed upper triangle, rewritten in place
+    float *D;                      // working matrix, rewritten in place: the packed
+                                   // upper triangle, or (full = 1) the symmetric n x n
+                                   // matrix row-major, both halves kept current
+    int full;
     long long n;
     int linkage;                   // 0 single, 1 complete, 2 average, 3 Ward
     int G;                         // CTAs in the persistent grid
@@ -114,6 +117,11 @@ struct BatchParams {
     long long *merges_done;        // total merges performed (optional)
     unsigned long long timeout_ns;
 };
+
+// Writes the symmetric n x n matrix `full` (row-major, diagonal untouched)
+// from the packed upper triangle `packed`, with -0 cells as +0; a NaN,
+// infinite or negative cell sets *status to kErrInput.
+cudaError_t launch_expand(const float *packed, float *full, long long n, int *status, cudaStream_t stream);
 
 // Bytes of dynamic shared memory the merge kernel needs for (n, G).
 size_t merge_smem_bytes(long long n, int G);

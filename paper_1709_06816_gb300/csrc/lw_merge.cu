@@ -85,6 +85,18 @@ __device__ __forceinline__ long long pair_idx(long long a, long long b, long lon
     return a < b ? tri_off(a, n) + (b - a - 1) : tri_off(b, n) + (a - b - 1);
 }
 
+// Row r of the working matrix: cell (r, c) at row_base + c (packed: c > r only).
+__device__ __forceinline__ long long row_base(const MergeParams &p, long long r)
+{
+    return p.full ? r * p.n : tri_off(r, p.n) - r - 1;
+}
+
+// Any copy of cell {x, y}, x != y.
+__device__ __forceinline__ long long cell_at(const MergeParams &p, long long x, long long y)
+{
+    return p.full ? x * p.n + y : pair_idx(x, y, p.n);
+}
+
 __device__ __forceinline__ u64 make_key(float v, unsigned c)
 {
     return ((u64)__float_as_uint(v) << 32) | (u64)c;
@@ -429,7 +441,7 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
 {
     const long long n = p.n;
     const int lane = threadIdx.x & 31;
-    const long long start = tri_off(r, n);
+    const long long start = row_base(p, r) + r + 1;
     const long long end = start + (n - r - 1);
     const long long base_c = r + 1 - start;  // column of flat index q is q + base_c
     u64 L[K];
@@ -480,7 +492,7 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
                                long long &live_cells)
 {
     const long long n = p.n;
-    const long long start = tri_off(r, n);
+    const long long start = row_base(p, r) + r + 1;
     const long long end = start + (n - r - 1);
     const long long base_c = r + 1 - start;
     u64 L[K];
@@ -884,7 +896,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 warp_topk(L, M);
                 // the new cells (row, i_a) of the previous round's merges, one lane each
                 const int np2 = sh.nprev;
-                const long long base = tri_off(row, n) - row - 1;  // cell (row, c) at base + c
+                const long long base = row_base(p, row);  // cell (row, c) at base + c
                 u64 xr = kNoKey;
                 if (lane < np2) {
                     const long long ia = sh.ppi[lane];
@@ -956,8 +968,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             sh.szi[tid] = __ldcg(p.size_g + sh.pi[tid]);
             sh.szj[tid] = __ldcg(p.size_g + sh.pj[tid]);
             const long long i = sh.pi[tid], j = sh.pj[tid];
-            sh.bi[tid] = tri_off(i, n) - i - 1;  // cell (i, c) at bi + c for c > i
-            sh.bj[tid] = tri_off(j, n) - j - 1;
+            sh.bi[tid] = row_base(p, i);  // cell (i, c) at bi + c (packed: for c > i)
+            sh.bj[tid] = row_base(p, j);
         }
         if (tid < 2 * s) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
@@ -969,7 +981,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (u < v && (u >> 1) != (v >> 1)) {
                 const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                 const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                const float d = __ldcg(p.D + pair_idx(mu, mv, n));
+                const float d = __ldcg(p.D + cell_at(p, mu, mv));
                 sh.Dm[u][v] = d;
                 sh.Dm[v][u] = d;
             }
@@ -1006,16 +1018,19 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     if (ok)
                         nk = rsize[l];
                 }
+                // cell (k, i): in the full matrix row i holds it (consecutive
+                // k of a warp read consecutive words); packed, row k for k < i
                 float va[S], vb[S];
-                const long long bk = tri_off(k, n) - k - 1;  // cell (k, c) at bk + c for c > k
+                const long long bk = row_base(p, k);
+                const bool full = p.full;
 #pragma unroll
                 for (int a = 0; a < S; ++a) {
                     va[a] = 0.0f;
                     vb[a] = 0.0f;
                     if (ok && a < s) {
                         const long long i = sh.pi[a], j = sh.pj[a];
-                        va[a] = __ldcg(p.D + (k < i ? bk + i : sh.bi[a] + k));
-                        vb[a] = __ldcg(p.D + (k < j ? bk + j : sh.bj[a] + k));
+                        va[a] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
+                        vb[a] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
                     }
                 }
 #pragma unroll
@@ -1078,8 +1093,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     rb = -1;
                 const long long qa = ra >= 0 ? first_block(ra) : my_blocks;
                 const long long qbb = rb >= 0 ? first_block(rb) : my_blocks;
-                const float *Da = p.D + (ra >= 0 ? tri_off(ra, n) - ra - 1 : 0);  // cell (ra, c) at Da[c]
-                const float *Db = p.D + (rb >= 0 ? tri_off(rb, n) - rb - 1 : 0);
+                const float *Da = p.D + (ra >= 0 ? row_base(p, ra) : 0);  // cell (ra, c) at Da[c]
+                const float *Db = p.D + (rb >= 0 ? row_base(p, rb) : 0);
                 u64 La[K], Lb[K];
 #pragma unroll
                 for (int q = 0; q < K; ++q) {
@@ -1223,8 +1238,11 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
             for (int e = tid; e < L * L; e += NT) {
                 const int a = e / L, c = e % L;
-                if (a < c)
-                    __stcg(p.D + pair_idx(sh.pi[a], sh.pi[c], n), sh.C[a][c]);
+                if (a < c) {
+                    __stcg(p.D + cell_at(p, sh.pi[a], sh.pi[c]), sh.C[a][c]);
+                    if (p.full)
+                        __stcg(p.D + cell_at(p, sh.pi[c], sh.pi[a]), sh.C[a][c]);
+                }
             }
             // each pair a < c stands for three updates of the step-by-step
             // order: merge a rewrites (i_a, i_c) and (i_a, j_c), merge c (i_c, i_a)
@@ -1326,7 +1344,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 // pairs the round did not merge, and rows past a thread's
                 // first, compute them now
                 const bool have = l0 == 0 && kok;
-                const long long bk = tri_off(k, n) - k - 1;  // cell (k, c) at bk + c for c > k
+                const long long bk = row_base(p, k);
+                const bool full = p.full;
                 float va[S], vb[S];
 #pragma unroll
                 for (int a = 0; a < S; ++a) {
@@ -1334,8 +1353,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     vb[a] = 0.0f;
                     if (!have && a < L) {
                         const long long i = sh.pi[a], j = sh.pj[a];
-                        va[a] = __ldcg(p.D + (k < i ? bk + i : sh.bi[a] + k));
-                        vb[a] = __ldcg(p.D + (k < j ? bk + j : sh.bj[a] + k));
+                        va[a] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
+                        vb[a] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
                     }
                 }
                 u64 Cc[K];
@@ -1349,7 +1368,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     const long long ia = sh.pi[a], ja = sh.pj[a];
                     const float v =
                         have ? kv[a] : lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                    __stcg(p.D + (k < ia ? bk + ia : sh.bi[a] + k), v);
+                    __stcg(p.D + (full || k > ia ? sh.bi[a] + k : bk + ia), v);
+                    if (full)
+                        __stcg(p.D + bk + ia, v);  // the copy in row k
                     ++st_updates;
                     if (k < ja) {
                         // row k loses column j; if k < i its cell (k, i) changed as well
@@ -1497,6 +1518,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
         const BatchJob J = bp.jobs[jb];
         MergeParams p;
         p.D = J.D;
+        p.full = 0;
         p.n = J.n;
         p.linkage = J.linkage;
         p.G = 1;
@@ -1524,7 +1546,53 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
         atomicAdd(reinterpret_cast<unsigned long long *>(bp.merges_done), (unsigned long long)merges_done);
 }
 
+// The symmetric matrix from the packed triangle, one 32 x 32 tile of the
+// upper triangle per CTA (32 x 8 threads): the tile is read row by row and
+// written both as it is and transposed through shared memory, so every
+// global access of a warp is 32 consecutive words.
+__global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ P, float *__restrict__ F,
+                                                     long long n, int *status)
+{
+    __shared__ float tile[32][33];
+    const long long tr = blockIdx.y, tc = blockIdx.x;
+    if (tr > tc)
+        return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    int bad = 0;
+    for (int yy = ty; yy < 32; yy += 8) {
+        const long long r = tr * 32 + yy, c = tc * 32 + tx;
+        float v = 0.0f;
+        if (c > r && c < n) {
+            v = __ldg(P + tri_off(r, n) + (c - r - 1));
+            const unsigned u = __float_as_uint(v);
+            if (u == 0x80000000u)
+                v = 0.0f;  // -0 reads as +0 from here on
+            else if (u > 0x7f7fffffu)
+                bad = 1;   // NaN, infinite or negative
+            F[r * n + c] = v;
+        }
+        tile[yy][tx] = v;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const long long c = tc * 32 + yy, r = tr * 32 + tx;
+        if (c > r && c < n)
+            F[c * n + r] = tile[tx][yy];
+    }
+    if (bad)
+        atomicCAS(status, 0, kErrInput);
+}
+
 }  // namespace
+
+cudaError_t launch_expand(const float *packed, float *full, long long n, int *status, cudaStream_t stream)
+{
+    const long long nb = (n + 31) / 32;
+    if (nb > 65535)
+        return cudaErrorInvalidValue;
+    expand_kernel<<<dim3((unsigned)nb, (unsigned)nb), dim3(32, 8), 0, stream>>>(packed, full, n, status);
+    return cudaGetLastError();
+}
 
 size_t merge_smem_bytes(long long n, int G)
 {

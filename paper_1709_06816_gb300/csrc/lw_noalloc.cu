@@ -102,6 +102,7 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
 
     lw::MergeParams p;
     p.D = dist;
+    p.full = 0;
     p.n = n;
     p.linkage = linkage;
     p.G = G;

@@ -187,6 +187,8 @@ struct lw_server {
         }
         lw_set_option(L.ctx, LW_OPT_GRID, grid_for(r.n));
         lw_set_option(L.ctx, LW_OPT_CTA_THREADS, threads_for(r.n));
+        // the pool's byte budget covers the packed matrices only
+        lw_set_option(L.ctx, LW_OPT_LAYOUT, 2);
         lw_status s = lw_cluster_async(L.ctx, d, r.n, r.linkage, dm, dh);
         if (s != LW_OK)
             return s;

@@ -31,7 +31,7 @@ EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_sta
            "lw_set_batch_classes",
            "lw_cluster_batch", "lw_server_create", "lw_server_submit", "lw_server_poll",
            "lw_server_drain", "lw_server_get_stats", "lw_server_destroy", "lw_cluster_noalloc")
-LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT, LW_OPT_CTA_THREADS = 4, 5, 6
+LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT, LW_OPT_CTA_THREADS, LW_OPT_LAYOUT = 4, 5, 6, 7
 
 
 class LwServerStats(ctypes.Structure):
@@ -348,6 +348,10 @@ class Context:
         s = load().lw_set_batch_classes(self.handle, nh, nt, k)
         if s != 0:
             raise LwError(s, f"lw_set_batch_classes({classes})")
+
+    def set_layout(self, layout: int):
+        """0 automatic, 1 symmetric n x n working copy, 2 packed triangle."""
+        lw_set_option(self.handle, LW_OPT_LAYOUT, layout)
 
     def set_cta_threads(self, nt: int):
         lw_set_option(self.handle, LW_OPT_CTA_THREADS, nt)

@@ -73,6 +73,24 @@ def test_small_multi_cta(ctx, link, grid):
                          f"n={n} grid={grid}")
 
 
+@pytest.mark.parametrize("layout", [1, 2])
+def test_layouts(ctx, layout):
+    """The symmetric n x n working copy (1) and the packed triangle (2), on one
+    CTA and on several, against the oracle."""
+    ctx.set_layout(layout)
+    try:
+        for s, n in enumerate([3, 33, 100, 257, 1000, 2100]):
+            for link in range(4):
+                D = synth.small_gmm(n, 500 + s) if (s + link) % 2 else synth.tie_heavy(n, 500 + s, levels=4)
+                want = oracle.cached(D, n, link)
+                for grid in (1, 7, 40):
+                    _assert_same(_gpu(ctx, D, n, link, grid=grid), want,
+                                 f"layout={layout} n={n} link={link} grid={grid}")
+    finally:
+        ctx.set_layout(0)
+        ctx.set_grid(0)
+
+
 @pytest.mark.parametrize("nt", [128, 256])
 def test_smaller_ctas(ctx, nt):
     """The merge kernel built for 128- and 256-thread CTAs, one CTA and several."""
