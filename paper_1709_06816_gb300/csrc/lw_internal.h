@@ -10,7 +10,8 @@ namespace lw {
 constexpr int kThreads = 512;            // default threads per CTA of the merge kernel
 constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
 constexpr int kCacheKeys = 4;            // smallest keys cached per row
-constexpr int kPub = 4;                  // entries a CTA publishes per round
+constexpr int kPub = 4;                  // entries a CTA of a multi-CTA grid publishes per round
+constexpr int kPubOne = 16;              // entries a job's only CTA publishes per round
 constexpr int kRound = 16;               // most merges one round certifies
 constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
 constexpr int kMaxReq = 128;             // refill requests served per round
@@ -26,16 +27,18 @@ constexpr unsigned kHardStop = 0x40000000u;  // the CTA published no entries bey
 // Status words written by the kernel (values match lw_status).
 enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
 
-// One CTA's record at the start of a round, 96 bytes: its kPub smallest
-// cache entries (key = (bits(value) << 32) | (row << 3) | rank, column word
-// beside it) and the rows (at most kReqPerCta) that ask for a refill.
+// One CTA's record at the start of a round, 240 bytes: its smallest cache
+// entries (kPub of them, kPubOne for a one-CTA job; key = (bits(value) << 32)
+// | (row << 3) | rank, column word beside it) and the rows (at most
+// kReqPerCta) that ask for a refill.
 struct __align__(16) RecA {
-    unsigned long long key[kPub];
-    unsigned int col[kPub];
+    unsigned long long key[kPubOne];
+    unsigned int col[kPubOne];
     int nreq;
     int req[kReqPerCta];
     int pad[3];
 };
+static_assert(sizeof(RecA) == 240, "record layout");
 
 struct MergeParams {
     float *D;                      // working matrix, rewritten in place: the packed

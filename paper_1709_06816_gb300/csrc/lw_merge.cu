@@ -178,20 +178,30 @@ __device__ __forceinline__ u64 warp_u64_min(u64 v)
     return ((u64)mhi << 32) | mlo;
 }
 
-// K smallest keys over the lists of a warp (keys are distinct or kNoKey).
-__device__ __forceinline__ void warp_topk(u64 (&L)[K], u64 (&out)[K])
+// KK smallest keys over the sorted lists of a warp (keys are distinct or kNoKey).
+template <int KK>
+__device__ __forceinline__ void warp_topk(u64 (&L)[KK], u64 (&out)[KK])
 {
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
+    for (int q = 0; q < KK; ++q) {
         const u64 m = warp_u64_min(L[0]);
         out[q] = m;
         if (m != kNoKey && L[0] == m) {
 #pragma unroll
-            for (int s = 0; s + 1 < K; ++s)
+            for (int s = 0; s + 1 < KK; ++s)
                 L[s] = L[s + 1];
-            L[K - 1] = kNoKey;
+            L[KK - 1] = kNoKey;
         }
     }
+}
+
+// Insert x into a sorted list of KK keys; the largest falls off.
+template <int KK>
+__device__ __forceinline__ void list_insert_n(u64 (&L)[KK], u64 x)
+{
+#pragma unroll
+    for (int q = 0; q < KK; ++q)
+        cswap(L[q], x);
 }
 
 // Candidate of the global minimum: (value, row) and column.
@@ -209,7 +219,7 @@ __device__ __forceinline__ void cand_min(Cand &x, const Cand &y)
 constexpr int S = kRound;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr u64 kHi = 0xffffffff00000000ull;
-static_assert(kPub == K, "a CTA publishes its entries with the K-list reductions");
+static_assert(kPub <= kPubOne && kPub % 4 == 0 && kPubOne % 4 == 0, "record layout");
 static_assert(K == 4, "sort_list is a 4-input network");
 static_assert(S == 16, "certification and pair minima use groups of 16 lanes");
 
@@ -263,8 +273,8 @@ __device__ __forceinline__ Cand cell_cand(unsigned vb, unsigned x, unsigned y)
 template <int NT>
 struct Shared {
     static constexpr int W = NT / 32;
-    u64 tk[W][K];
-    u64 tko[K];
+    u64 tk[W][kPubOne];
+    u64 tko[kPubOne];
     int wcnt[W];
     int flag;
     int nexec;                   // refill rows served this round
@@ -335,28 +345,28 @@ __device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, S
     __syncthreads();
 }
 
-// K smallest keys over every thread's list; result in sh.tko (all threads).
-template <int NT>
-__device__ void block_topk(u64 (&L)[K], Shared<NT> &sh)
+// KK smallest keys over every thread's sorted list; result in sh.tko (all threads).
+template <int NT, int KK>
+__device__ void block_topk(u64 (&L)[KK], Shared<NT> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u64 w[K];
+    u64 w[KK];
     warp_topk(L, w);
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+        for (int q = 0; q < KK; ++q)
             sh.tk[warp][q] = w[q];
     }
     __syncthreads();
     if (warp == 0) {
-        u64 M[K];
+        u64 M[KK];
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+        for (int q = 0; q < KK; ++q)
             M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
         warp_topk(M, w);
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < K; ++q)
+            for (int q = 0; q < KK; ++q)
                 sh.tko[q] = w[q];
         }
     }
@@ -522,10 +532,46 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
     block_topk(L, sh);
 }
 
+// K smallest keys of row r over live columns, computed by one warp (the
+// rows of a one-CTA job are refreshed this way, several warps side by side).
+// Adds the live cells read to `live_cells`.  Result in out (all lanes).
+__device__ void warp_row_refresh(const MergeParams &p, long long r, const unsigned *bitmap, u64 (&out)[K],
+                                 long long &live_cells)
+{
+    const int lane = threadIdx.x & 31;
+    const long long start = row_base(p, r) + r + 1;
+    const long long end = start + (p.n - r - 1);
+    const long long base_c = r + 1 - start;
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
+    long long cnt = 0;
+    for (long long q0 = start + lane; q0 < end; q0 += 8 * 32) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long q = q0 + 32 * u;
+            v[u] = q < end ? __ldcg(p.D + q) : -1.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long c = q0 + 32 * u + base_c;
+            if (v[u] >= 0.0f && live(bitmap, c)) {
+                ++cnt;
+                if (__float_as_uint(v[u]) <= (unsigned)(L[K - 1] >> 32))
+                    list_insert(L, make_key(v[u], (unsigned)c));
+            }
+        }
+    }
+    live_cells += cnt;
+    warp_topk(L, out);
+}
+
 // All n - 1 merges of one job, run by CTA b of the job's G CTAs (every CTA
 // of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
 // bytes of dynamic shared memory.
-template <int NT>
+template <int NT, int PUB>
 __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared<NT> &sh)
 {
     constexpr int W = NT / 32;
@@ -548,13 +594,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     unsigned *bitmap = reinterpret_cast<unsigned *>(q0);
     q0 += (nwords * 4 + 15) & ~15LL;
     u64 *wkey = reinterpret_cast<u64 *>(q0);
-    q0 += (size_t)G * K * 8;
+    q0 += (size_t)G * PUB * 8;
     u64 *ck = reinterpret_cast<u64 *>(q0);
     q0 += (size_t)Rmax * K * 8;
     u64 *cB = reinterpret_cast<u64 *>(q0);
     q0 += (size_t)Rmax * 8;
     unsigned *wcol = reinterpret_cast<unsigned *>(q0);
-    q0 += (size_t)G * K * 4;
+    q0 += (size_t)G * PUB * 4;
     int *hd = reinterpret_cast<int *>(q0);
     q0 += ((size_t)G * 4 + 15) & ~(size_t)15;
     int *rsize = reinterpret_cast<int *>(q0);
@@ -605,32 +651,32 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     long long st_updates = 0, st_fill_cells = 0, st_rescans = 0, st_resc_cells = 0;
     long long st_fills = 0, st_installs = 0, st_rounds = 0, st_idle = 0, st_walk = 0;
 
-    // The records of round rr: this CTA's kPub smallest entries (cached keys
+    // The records of round rr: this CTA's PUB smallest entries (cached keys
     // and bound marks of its rows) and its refill requests of round rr - 1.
     // Also lists the refills to install in round rr (served in round rr - 1).
     auto publish = [&](int rr) {
-        u64 Lst[K];
+        u64 Lst[PUB];
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+        for (int q = 0; q < PUB; ++q)
             Lst[q] = kNoKey;
         for (int l = tid; l < R; l += NT) {
             const int c = ccnt[l];
             const u64 B = cB[l];
             if (c > 0 || B != kNoKey) {
                 const u64 rowbits = (u64)row_of(l) << 3;
-                // a row's entries ascend: stop at the first one that cannot enter
+                // a row's entries ascend: skip the ones that cannot enter
 #pragma unroll
                 for (int q = 0; q < K; ++q) {
                     if (q < c) {
                         const u64 e = (ck[(size_t)q * Rmax + l] & kHi) | rowbits | (u64)q;
-                        if (e < Lst[K - 1])
-                            list_insert(Lst, e);
+                        if (e < Lst[PUB - 1])
+                            list_insert_n(Lst, e);
                     }
                 }
                 if (B != kNoKey) {
                     const u64 e = (B & kHi) | rowbits | (u64)c;
-                    if (e < Lst[K - 1])
-                        list_insert(Lst, e);
+                    if (e < Lst[PUB - 1])
+                        list_insert_n(Lst, e);
                 }
             }
             if (rr >= 2 && pend_t[l] == rr - 2) {
@@ -639,22 +685,22 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         block_topk(Lst, sh);
-        if (tid == 0) {
-            unsigned cols[K];
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const u64 key = sh.tko[q];
-                unsigned col = 0;
-                if (key != kNoKey) {
-                    const unsigned lo = (unsigned)key;
-                    const int slot = slot_of((long long)(lo >> 3));
-                    const int rank = (int)(lo & 7u);
-                    col = rank < ccnt[slot] ? (unsigned)ck[(size_t)rank * Rmax + slot] : kRowStop;
-                    if (q == K - 1)
-                        col |= kHardStop;  // more entries may follow: none is published
-                }
-                cols[q] = col;
+        if (tid < PUB) {
+            // entry tid: its column word
+            const u64 key = sh.tko[tid];
+            unsigned col = 0;
+            if (key != kNoKey) {
+                const unsigned lo = (unsigned)key;
+                const int slot = slot_of((long long)(lo >> 3));
+                const int rank = (int)(lo & 7u);
+                col = rank < ccnt[slot] ? (unsigned)ck[(size_t)rank * Rmax + slot] : kRowStop;
+                if (tid == PUB - 1)
+                    col |= kHardStop;  // more entries may follow: none is published
             }
+            __stcg(&p.recA[b].key[tid], key);
+            __stcg(&p.recA[b].col[tid], col);
+        }
+        if (tid == 0) {
             const int par = (rr - 1) & 1;
             int nq = rr >= 1 ? sh.nmyreq[par] : 0;
             nq = nq < kReqPerCta ? nq : kReqPerCta;
@@ -664,15 +710,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
 #pragma unroll
             for (int q = 0; q < kReqPerCta; ++q)
                 rows[q] = q < nq ? (int)row_of(sh.myreq_l[par][q]) : -1;
-            uint4 *dst = reinterpret_cast<uint4 *>(p.recA + b);
-            __stcg(dst + 0, make_uint4((unsigned)sh.tko[0], (unsigned)(sh.tko[0] >> 32),
-                                       (unsigned)sh.tko[1], (unsigned)(sh.tko[1] >> 32)));
-            __stcg(dst + 1, make_uint4((unsigned)sh.tko[2], (unsigned)(sh.tko[2] >> 32),
-                                       (unsigned)sh.tko[3], (unsigned)(sh.tko[3] >> 32)));
-            __stcg(dst + 2, make_uint4(cols[0], cols[1], cols[2], cols[3]));
-            __stcg(dst + 3, make_uint4((unsigned)nq, (unsigned)rows[0], (unsigned)rows[1], (unsigned)rows[2]));
-            __stcg(dst + 4, make_uint4((unsigned)rows[3], (unsigned)rows[4], (unsigned)rows[5], (unsigned)rows[6]));
-            __stcg(dst + 5, make_uint4((unsigned)rows[7], 0u, 0u, 0u));
+            uint4 *dst = reinterpret_cast<uint4 *>(&p.recA[b].nreq);
+            __stcg(dst + 0, make_uint4((unsigned)nq, (unsigned)rows[0], (unsigned)rows[1], (unsigned)rows[2]));
+            __stcg(dst + 1, make_uint4((unsigned)rows[3], (unsigned)rows[4], (unsigned)rows[5], (unsigned)rows[6]));
+            __stcg(dst + 2, make_uint4((unsigned)rows[7], 0u, 0u, 0u));
         }
     };
 
@@ -757,18 +798,26 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             for (int q = 0; q < kReqPerCta; ++q)
                 rq[q] = -1;
             if (tid < G) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.recA + tid);
-                const uint4 w0 = __ldcg(src), w1 = __ldcg(src + 1), w2 = __ldcg(src + 2);
-                const uint4 w3 = __ldcg(src + 3), w4 = __ldcg(src + 4), w5 = __ldcg(src + 5);
-                wkey[tid * K + 0] = ((u64)w0.y << 32) | w0.x;
-                wkey[tid * K + 1] = ((u64)w0.w << 32) | w0.z;
-                wkey[tid * K + 2] = ((u64)w1.y << 32) | w1.x;
-                wkey[tid * K + 3] = ((u64)w1.w << 32) | w1.z;
-                wcol[tid * K + 0] = w2.x;
-                wcol[tid * K + 1] = w2.y;
-                wcol[tid * K + 2] = w2.z;
-                wcol[tid * K + 3] = w2.w;
+                const RecA *rec = p.recA + tid;
+                const ulonglong2 *ks = reinterpret_cast<const ulonglong2 *>(rec->key);
+#pragma unroll
+                for (int q = 0; q < PUB / 2; ++q) {
+                    const ulonglong2 kk = __ldcg(ks + q);
+                    wkey[tid * PUB + 2 * q] = kk.x;
+                    wkey[tid * PUB + 2 * q + 1] = kk.y;
+                }
+                const uint4 *cs = reinterpret_cast<const uint4 *>(rec->col);
+#pragma unroll
+                for (int q = 0; q < PUB / 4; ++q) {
+                    const uint4 cc = __ldcg(cs + q);
+                    wcol[tid * PUB + 4 * q] = cc.x;
+                    wcol[tid * PUB + 4 * q + 1] = cc.y;
+                    wcol[tid * PUB + 4 * q + 2] = cc.z;
+                    wcol[tid * PUB + 4 * q + 3] = cc.w;
+                }
                 hd[tid] = 0;
+                const uint4 *src = reinterpret_cast<const uint4 *>(&rec->nreq);
+                const uint4 w3 = __ldcg(src), w4 = __ldcg(src + 1), w5 = __ldcg(src + 2);
                 rcnt = (int)w3.x;
                 rq[0] = (int)w3.y;
                 rq[1] = (int)w3.z;
@@ -804,7 +853,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             u64 lm = kNoKey;
             int lg = -1;
             for (int g = lane; g < G; g += 32) {
-                const u64 k0 = wkey[g * K];
+                const u64 k0 = wkey[g * PUB];
                 if (k0 < lm) {
                     lm = k0;
                     lg = g;
@@ -813,7 +862,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             int np = 0;
             int member = -1;  // lane 2a holds i_a, lane 2a + 1 holds j_a
             unsigned front = 0;  // value bits of the last entry visited
-            for (int guard = 0; guard <= G * K; ++guard) {
+            for (int guard = 0; guard <= G * PUB; ++guard) {
                 const u64 m = warp_u64_min(lm);
                 if (m == kNoKey)
                     break;
@@ -823,14 +872,14 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 unsigned col = 0;
                 if (lane == src) {
                     const int h = hd[lg];
-                    col = wcol[lg * K + h];
+                    col = wcol[lg * PUB + h];
                     hd[lg] = h + 1;
                     lm = kNoKey;
                     lg = -1;
                     for (int g = lane; g < G; g += 32) {
                         const int hh = hd[g];
-                        if (hh < K) {
-                            const u64 kk = wkey[g * K + hh];
+                        if (hh < PUB) {
+                            const u64 kk = wkey[g * PUB + hh];
                             if (kk < lm) {
                                 lm = kk;
                                 lg = g;
@@ -1268,7 +1317,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 pend_t[l] = -1;
             }
             const long long ia = sh.pi[a];
-            if (owner_of(ia) == b) {
+            if (G == 1) {
+                // a job's only CTA sees every write after pass 2: it rescans
+                // the survivor row then
+                const int l = slot_of(ia);
+                ccnt[l] = 0;
+                cB[l] = kNoKey;
+                rsize[l] = sh.szi[a] + sh.szj[a];
+                pend_t[l] = -1;
+                rlist[atomicAdd(&sh.nresc, 1)] = l;
+            } else if (owner_of(ia) == b) {
                 // the survivor's cache: its smallest new cell outside the chain
                 // and, below it, the new cells to chain members
                 const int l = slot_of(ia);
@@ -1402,7 +1460,11 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 cache_store(l, Cc);
                 ccnt[l] = c;
                 cB[l] = B;
-                if (c == 0 && B != kNoKey && (unsigned)(B >> 32) <= sh.front) {
+                if (G == 1) {
+                    // one CTA: no one else to ask, refill right after this pass
+                    if (c <= kRefillAt && B != kNoKey)
+                        rlist[atomicAdd(&sh.nresc, 1)] = l;
+                } else if (c == 0 && B != kNoKey && (unsigned)(B >> 32) <= sh.front) {
                     // live cells remain, none is cached, and the bound sits at
                     // the front of the merges: its bare stop mark would hold
                     // the next rounds up until a refill lands, so rescan now
@@ -1415,8 +1477,25 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         __syncthreads();
-        // ---- rows whose cache emptied
-        {
+        // ---- rows whose cache emptied (one-CTA job: also survivors and rows
+        // running low, a warp each)
+        if (G == 1) {
+            const int nresc = sh.nresc;
+            for (int q = warp; q < nresc; q += W) {
+                const int l = rlist[q];
+                u64 top[K];
+                warp_row_refresh(p, row_of(l), bitmap, top, st_resc_cells);
+                if (lane == 0) {
+                    cache_store(l, top);
+                    const int c = list_count(top);
+                    ccnt[l] = c;
+                    cB[l] = c == K ? top[K - 1] : kNoKey;
+                }
+            }
+            st_rescans += nresc;
+            if (nresc > 0)
+                __syncthreads();
+        } else {
             const int nresc = sh.nresc;
             for (int q = 0; q < nresc; ++q) {
                 const int l = rlist[q];
@@ -1487,12 +1566,12 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     }
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, int PUB>
 __global__ void __launch_bounds__(NT, MINB) merge_kernel(MergeParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared<NT> sh;
-    merge_job<NT>(p, blockIdx.x, smem_raw, sh);
+    merge_job<NT, PUB>(p, blockIdx.x, smem_raw, sh);
 }
 
 // Many independent jobs in one persistent launch: each CTA takes the next job
@@ -1535,7 +1614,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
             reinterpret_cast<int *>(ws + L.zero)[q] = 0;
         __syncthreads();
         if (J.n > 1)
-            merge_job<NT>(p, 0, smem_raw, sh);
+            merge_job<NT, kPubOne>(p, 0, smem_raw, sh);
         __syncthreads();
         if (threadIdx.x == 0) {
             bp.job_status[jb] = J.n > 1 ? __ldcg(p.status) : 0;
@@ -1601,19 +1680,28 @@ size_t merge_smem_bytes(long long n, int G)
     const long long nwords = (n + 31) / 32;
     // bitmap; published entries (keys, column words, walk positions); per
     // slot: K keys, bound, size, count, refill round and position, chain flag
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * K * 12 + (((long long)G * 4 + 15) & ~15LL) +
+    const long long pub = G == 1 ? kPubOne : kPub;
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + (((long long)G * 4 + 15) & ~15LL) +
                     Rmax * (8 * K + 8 + 4 * 5 + 1));
 }
 
 namespace {
 
 // The kernel instantiations: CTA size nt and the CTAs per SM its registers allow.
-const void *merge_fn(int nt)
+// A one-CTA job publishes more entries per round (nothing else is read).
+const void *merge_fn(int nt, int G)
 {
+    if (G == 1) {
+        switch (nt) {
+        case 128: return (const void *)merge_kernel<128, 4, kPubOne>;
+        case 256: return (const void *)merge_kernel<256, 2, kPubOne>;
+        default: return (const void *)merge_kernel<512, 1, kPubOne>;
+        }
+    }
     switch (nt) {
-    case 128: return (const void *)merge_kernel<128, 4>;
-    case 256: return (const void *)merge_kernel<256, 2>;
-    default: return (const void *)merge_kernel<512, 1>;
+    case 128: return (const void *)merge_kernel<128, 4, kPub>;
+    case 256: return (const void *)merge_kernel<256, 2, kPub>;
+    default: return (const void *)merge_kernel<512, 1, kPub>;
     }
 }
 
@@ -1659,7 +1747,7 @@ bool merge_config_ok(long long n, int G, int num_sms, int nt)
     // the first G threads read the CTAs' records
     if (G < 1 || G > num_sms || G > nt)
         return false;
-    return fit_per_sm(merge_fn(nt), nt, merge_smem_bytes(n, G)) >= 1;
+    return fit_per_sm(merge_fn(nt, G), nt, merge_smem_bytes(n, G)) >= 1;
 }
 
 int batch_ctas_per_sm(long long n_max, int nt)
@@ -1680,7 +1768,7 @@ cudaError_t launch_batch(const BatchParams &bp, int grid, int nt, cudaStream_t s
 cudaError_t launch_merge(const MergeParams &p, int nt, cudaStream_t stream)
 {
     const size_t smem = merge_smem_bytes(p.n, p.G);
-    const void *fn = merge_fn(nt);
+    const void *fn = merge_fn(nt, p.G);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
