@@ -54,7 +54,7 @@ struct MergeParams {
     int *size_g;                   // [n] cluster sizes
     RecA *recA;                    // [G] published entries and refill requests
     unsigned long long *recB;      // [G][2][kRound] per-pair minima of the new cells
-    unsigned long long *parts;     // [2][G][kMaxReq][kCacheKeys] refill partial top-K
+    unsigned long long *parts;     // [2][kMaxReq][kCacheKeys] refill lists (top-K of a row)
     unsigned int *bar;             // grid barrier counter (zero at launch)
     int *status;                   // [4] status word [0]; barrier that gave up [1]
     long long *stats;              // [kStats] counters, see lw_get_stats
@@ -80,7 +80,7 @@ __host__ __device__ inline WorkspaceLayout workspace_layout(long long n, int G)
     L.size = off;   off = up(off + sizeof(int) * (size_t)n);
     L.recA = off;   off = up(off + sizeof(RecA) * (size_t)G);
     L.recB = off;   off = up(off + 8 * 2 * kRound * (size_t)G);
-    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 2 * (size_t)G);
+    L.parts = off;  off = up(off + 8 * kCacheKeys * (size_t)kMaxReq * 2);
     L.zero = off;
     L.bar = off;    off = up(off + 256);
     L.status = off; off = up(off + 4 * sizeof(int));

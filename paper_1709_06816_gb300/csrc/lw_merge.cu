@@ -494,9 +494,9 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
     warp_topk(L, out);
 }
 
-// K smallest keys of row r over live columns, computed by the whole CTA
-// (for a row whose cache empties before a refill arrives).  Adds the live
-// cells read to `live_cells`.  Result in sh.tko.
+// K smallest keys of row r over live columns, computed by the whole CTA (a
+// refill, or a row whose cache emptied).  Adds the live cells read to
+// `live_cells`.  Result in sh.tko.
 template <int NT>
 __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT> &sh,
                                long long &live_cells)
@@ -510,21 +510,42 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
     for (int q = 0; q < K; ++q)
         L[q] = kNoKey;
     long long cnt = 0;
-    // eight loads in flight per thread
-    for (long long q0 = start + threadIdx.x; q0 < end; q0 += 8 * NT) {
-        float v[8];
+    auto take = [&](float v, long long q) {
+        const long long c = q + base_c;
+        if (live(bitmap, c)) {
+            ++cnt;
+            if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
+                list_insert(L, make_key(v, (unsigned)c));
+        }
+    };
+    // unaligned head and tail one word per thread; the body as 16-byte loads,
+    // eight in flight per thread (dead cells are read and dropped: the row is
+    // contiguous, latency and not bandwidth bounds the scan)
+    long long a0 = p.aligned16 ? ((start + 3) & ~3LL) : end;
+    if (a0 > end)
+        a0 = end;
+    const long long a1 = a0 + ((end - a0) & ~3LL);
+    for (long long q = start + threadIdx.x; q < a0; q += NT)
+        take(__ldcg(p.D + q), q);
+    for (long long q = a1 + threadIdx.x; q < end; q += NT)
+        take(__ldcg(p.D + q), q);
+    const float4 *D4 = reinterpret_cast<const float4 *>(p.D);
+    const long long j1 = a1 >> 2;
+    for (long long j0 = (a0 >> 2) + threadIdx.x; j0 < j1; j0 += 8 * NT) {
+        float4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const long long q = q0 + (long long)u * NT;
-            v[u] = q < end ? __ldcg(p.D + q) : -1.0f;
+            const long long j = j0 + (long long)u * NT;
+            v[u] = j < j1 ? __ldcg(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const long long c = q0 + (long long)u * NT + base_c;
-            if (v[u] >= 0.0f && live(bitmap, c)) {
-                ++cnt;
-                if (__float_as_uint(v[u]) <= (unsigned)(L[K - 1] >> 32))
-                    list_insert(L, make_key(v[u], (unsigned)c));
+            if (v[u].x >= 0.0f) {
+                const long long q = (j0 + (long long)u * NT) << 2;
+                take(v[u].x, q);
+                take(v[u].y, q + 1);
+                take(v[u].z, q + 2);
+                take(v[u].w, q + 3);
             }
         }
     }
@@ -547,20 +568,39 @@ __device__ void warp_row_refresh(const MergeParams &p, long long r, const unsign
     for (int q = 0; q < K; ++q)
         L[q] = kNoKey;
     long long cnt = 0;
-    for (long long q0 = start + lane; q0 < end; q0 += 8 * 32) {
-        float v[8];
+    auto take = [&](float v, long long q) {
+        const long long c = q + base_c;
+        if (live(bitmap, c)) {
+            ++cnt;
+            if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
+                list_insert(L, make_key(v, (unsigned)c));
+        }
+    };
+    long long a0 = p.aligned16 ? ((start + 3) & ~3LL) : end;
+    if (a0 > end)
+        a0 = end;
+    const long long a1 = a0 + ((end - a0) & ~3LL);
+    for (long long q = start + lane; q < a0; q += 32)
+        take(__ldcg(p.D + q), q);
+    for (long long q = a1 + lane; q < end; q += 32)
+        take(__ldcg(p.D + q), q);
+    const float4 *D4 = reinterpret_cast<const float4 *>(p.D);
+    const long long j1 = a1 >> 2;
+    for (long long j0 = (a0 >> 2) + lane; j0 < j1; j0 += 8 * 32) {
+        float4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const long long q = q0 + 32 * u;
-            v[u] = q < end ? __ldcg(p.D + q) : -1.0f;
+            const long long j = j0 + 32 * u;
+            v[u] = j < j1 ? __ldcg(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const long long c = q0 + 32 * u + base_c;
-            if (v[u] >= 0.0f && live(bitmap, c)) {
-                ++cnt;
-                if (__float_as_uint(v[u]) <= (unsigned)(L[K - 1] >> 32))
-                    list_insert(L, make_key(v[u], (unsigned)c));
+            if (v[u].x >= 0.0f) {
+                const long long q = (j0 + 32 * u) << 2;
+                take(v[u].x, q);
+                take(v[u].y, q + 1);
+                take(v[u].z, q + 2);
+                take(v[u].w, q + 3);
             }
         }
     }
@@ -919,30 +959,26 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 sh.front = front;
             }
         } else {
-            // ---- refills served in the previous round: merge the partial
-            // lists, then replay that round's merges (the scan ran before
-            // them, or while they were being written)
+            // ---- refills served in the previous round: take the row's list,
+            // then replay that round's merges (the scan ran before them, or
+            // while they were being written)
             const int ninst = sh.ninst;
             const int ipar = par ^ 1;
             for (int s2 = warp - 1; s2 < ninst; s2 += W - 1) {
                 const int l = sh.inst_slot[s2];
                 const int pos = pend_s[l];
                 const long long row = row_of(l);
-                u64 L[K];
-#pragma unroll
-                for (int q = 0; q < K; ++q)
-                    L[q] = kNoKey;
-                for (int g = lane; g < G; g += 32) {
-                    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(
-                        p.parts + (((size_t)ipar * G + g) * kMaxReq + pos) * K);
-                    const ulonglong2 v0 = __ldcg(src), v1 = __ldcg(src + 1);
-                    list_insert(L, v0.x);
-                    list_insert(L, v0.y);
-                    list_insert(L, v1.x);
-                    list_insert(L, v1.y);
-                }
                 u64 M[K];
-                warp_topk(L, M);
+                {
+                    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(
+                        p.parts + ((size_t)ipar * kMaxReq + pos) * K);
+#pragma unroll
+                    for (int q = 0; q < K / 2; ++q) {
+                        const ulonglong2 v = __ldcg(src + q);
+                        M[2 * q] = v.x;
+                        M[2 * q + 1] = v.y;
+                    }
+                }
                 // the new cells (row, i_a) of the previous round's merges, one lane each
                 const int np2 = sh.nprev;
                 const long long base = row_base(p, row);  // cell (row, c) at base + c
@@ -956,19 +992,21 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
 #pragma unroll
                 for (int a = 0; a < S; ++a)
                     xs[a] = __shfl_sync(kFull, xr, a);
-                if (lane == 0) {
-                    int c = list_count(M);
-                    u64 B = c == K ? M[K - 1] : kNoKey;
+                // keys whose column a merge of that round retired or rewrote
+                const int c0 = list_count(M);
+                const u64 B0 = c0 == K ? M[K - 1] : kNoKey;
+                const int mi = lane < np2 ? sh.ppi[lane] : -1;
+                const int mj = lane < np2 ? sh.ppj[lane] : -1;
 #pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const int col = (int)(unsigned)M[q];
-                        for (int a = 0; a < np2; ++a) {
-                            if (M[q] != kNoKey && (col == sh.ppi[a] || col == sh.ppj[a]))
-                                M[q] = kNoKey;
-                        }
-                    }
+                for (int q = 0; q < K; ++q) {
+                    const int col = (int)(unsigned)M[q];
+                    if (__any_sync(kFull, M[q] != kNoKey && (col == mi || col == mj)))
+                        M[q] = kNoKey;
+                }
+                if (lane == 0) {
+                    u64 B = B0;
                     sort_list(M);
-                    c = list_count(M);
+                    int c = list_count(M);
 #pragma unroll
                     for (int a = 0; a < S; ++a) {
                         const u64 x = xs[a];
@@ -1122,79 +1160,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         grid_arrive(p, epoch);
 
         // ---- window of barrier B: serve the refills asked for in round r - 1,
-        // two rows per warp at a time: the K smallest keys of each row over
-        // this CTA's live columns.  Nobody rewrites a cell before the barrier
-        // except the cells of this round's merges, which the install replays.
+        // one CTA per row (row s of the list by CTA s mod G, all its threads):
+        // the K smallest keys of the row over live columns.  Nobody rewrites a
+        // cell before the barrier except the cells of this round's merges,
+        // which the install replays.
         {
             const int nexec = sh.nexec;
-            // first block of this CTA holding a column > rr
-            auto first_block = [&](long long rr) -> long long {
-                const long long blk = (rr + 1) / kRowBlock;
-                return blk <= b ? 0 : (blk - b + G - 1) / G;
-            };
-            for (int s0 = warp; s0 < nexec; s0 += 2 * W) {
-                const int s1 = s0 + W;
-                long long ra = sh.exec_row[s0];
-                long long rb = s1 < nexec ? sh.exec_row[s1] : -1;
-                if (ra < 0 || ra >= n - 1)
-                    ra = -1;
-                if (rb < 0 || rb >= n - 1)
-                    rb = -1;
-                const long long qa = ra >= 0 ? first_block(ra) : my_blocks;
-                const long long qbb = rb >= 0 ? first_block(rb) : my_blocks;
-                const float *Da = p.D + (ra >= 0 ? row_base(p, ra) : 0);  // cell (ra, c) at Da[c]
-                const float *Db = p.D + (rb >= 0 ? row_base(p, rb) : 0);
-                u64 La[K], Lb[K];
-#pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    La[q] = kNoKey;
-                    Lb[q] = kNoKey;
-                }
-                long long cnt = 0;
-                for (long long q0 = qa < qbb ? qa : qbb; q0 < my_blocks; q0 += 8) {
-                    float va[8], vb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const long long qq = q0 + u;
-                        const long long c = ((long long)b + (long long)G * qq) * kRowBlock + lane;
-                        const bool in = qq < my_blocks && c < n;
-                        va[u] = (in && qq >= qa && c > ra) ? __ldcg(Da + c) : -1.0f;
-                        vb[u] = (in && qq >= qbb && c > rb) ? __ldcg(Db + c) : -1.0f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        // dead columns were read too (their cells are stale, not
-                        // out of bounds) and are dropped here
-                        const unsigned c = (unsigned)(((long long)b + (long long)G * (q0 + u)) * kRowBlock + lane);
-                        if ((va[u] >= 0.0f || vb[u] >= 0.0f) && live(bitmap, c)) {
-                            if (va[u] >= 0.0f) {
-                                ++cnt;
-                                if (__float_as_uint(va[u]) <= (unsigned)(La[K - 1] >> 32))
-                                    list_insert(La, make_key(va[u], c));
-                            }
-                            if (vb[u] >= 0.0f) {
-                                ++cnt;
-                                if (__float_as_uint(vb[u]) <= (unsigned)(Lb[K - 1] >> 32))
-                                    list_insert(Lb, make_key(vb[u], c));
-                            }
-                        }
-                    }
-                }
-                st_fill_cells += cnt;
-                u64 w[K];
-                warp_topk(La, w);
-                if (lane < K / 2 && ra >= 0) {
-                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
-                        p.parts + (((size_t)par * G + b) * kMaxReq + s0) * K);
-                    __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
-                }
-                if (s1 < nexec) {
-                    warp_topk(Lb, w);
-                    if (lane < K / 2 && rb >= 0) {
-                        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(
-                            p.parts + (((size_t)par * G + b) * kMaxReq + s1) * K);
-                        __stcg(dst + lane, make_ulonglong2(w[2 * lane], w[2 * lane + 1]));
-                    }
+            for (int s2 = b; s2 < nexec; s2 += G) {
+                const long long rr = sh.exec_row[s2];
+                if (rr < 0 || rr >= n - 1)
+                    continue;  // the same for every thread of the CTA
+                block_row_topk(p, rr, bitmap, sh, st_fill_cells);
+                if (tid < K / 2) {
+                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.parts + ((size_t)par * kMaxReq + s2) * K);
+                    __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
                 }
             }
             st_fills += nexec;
