@@ -279,7 +279,6 @@ struct Shared {
     int flag;
     int nexec;                   // refill rows served this round
     int exec_row[kMaxReq];
-    int my_off;                  // where this CTA's requests landed in the list
     int nmyreq[2];               // this CTA's requests, by round parity
     int myreq_l[2][kReqPerCta];
     int ninst;                   // refills to install at the start of the next round
@@ -307,10 +306,11 @@ struct Shared {
 // After barrier A: the list of rows to refill in this round -- every CTA's
 // requests in CTA order (deterministic, the same in every CTA), cut at
 // kMaxReq.  Thread t holds CTA t's request count and rows.  Sets
-// sh.exec_row, sh.nexec and sh.my_off (the position of this CTA's first
-// request).
+// sh.exec_row and sh.nexec; thread b gives this CTA's own requests (list
+// pq) their list positions.
 template <int NT>
-__device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh)
+__device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh, int pq,
+                                  int *pend_t, int *pend_s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = cnt;
@@ -332,8 +332,16 @@ __device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, S
         if (q < cnt && off0 + q < kMaxReq)
             sh.exec_row[off0 + q] = rq[q];
     }
-    if ((int)threadIdx.x == b)
-        sh.my_off = off0;
+    if ((int)threadIdx.x == b) {
+        // this CTA's own requests (list pq) get their positions
+        for (int q = 0; q < cnt; ++q) {
+            const int l = sh.myreq_l[pq][q];
+            if (off0 + q < kMaxReq)
+                pend_s[l] = off0 + q;
+            else
+                pend_t[l] = -1;  // not served: the row may ask again
+        }
+    }
     if (warp == 0) {
         int tot = lane < (NT / 32) ? sh.wcnt[lane] : 0;
 #pragma unroll
@@ -626,7 +634,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     const long long nwords = (n + 31) / 32;
 
     // dynamic shared memory: liveness bitmap; the published entries of every
-    // CTA (keys, column words, walk positions); then per owned slot l: cache
+    // CTA (keys, column words); then per owned slot l: cache
     // keys (key q of slot l at ck[q * Rmax + l]: consecutive threads read
     // consecutive words), bound, size, key count, pending refill (round,
     // list position) and a flag for rows in this round's chain
@@ -641,8 +649,6 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     q0 += (size_t)Rmax * 8;
     unsigned *wcol = reinterpret_cast<unsigned *>(q0);
     q0 += (size_t)G * PUB * 4;
-    int *hd = reinterpret_cast<int *>(q0);
-    q0 += ((size_t)G * 4 + 15) & ~(size_t)15;
     int *rsize = reinterpret_cast<int *>(q0);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
@@ -855,7 +861,6 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     wcol[tid * PUB + 4 * q + 2] = cc.z;
                     wcol[tid * PUB + 4 * q + 3] = cc.w;
                 }
-                hd[tid] = 0;
                 const uint4 *src = reinterpret_cast<const uint4 *>(&rec->nreq);
                 const uint4 w3 = __ldcg(src), w4 = __ldcg(src + 1), w5 = __ldcg(src + 2);
                 rcnt = (int)w3.x;
@@ -868,37 +873,38 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 rq[6] = (int)w4.w;
                 rq[7] = (int)w5.x;
             }
-            exchange_requests(rcnt, rq, b, sh);
+            exchange_requests(rcnt, rq, b, sh, par ^ 1, pend_t, pend_s);
         }
-        // this CTA's requests of round r - 1 now have list positions
-        {
-            const int pq = par ^ 1;
-            const int nmy = r >= 1 ? sh.nmyreq[pq] : 0;
-            if (tid < nmy) {
-                const int l = sh.myreq_l[pq][tid];
-                const int pos = sh.my_off + tid;
-                if (pos < kMaxReq)
-                    pend_s[l] = pos;
-                else
-                    pend_t[l] = -1;  // not served: the row may ask again
-            }
-        }
-        __syncthreads();
         if (tid == 0)
             sh.nmyreq[par] = 0;
         lap(ph1);
 
         if (warp == 0) {
-            // ---- the walk: merge the G published lists in key order
-            u64 lm = kNoKey;
-            int lg = -1;
-            for (int g = lane; g < G; g += 32) {
-                const u64 k0 = wkey[g * PUB];
-                if (k0 < lm) {
-                    lm = k0;
-                    lg = g;
-                }
+            // ---- the walk: merge the G published lists in key order.  Lane
+            // l keeps the heads of the lists of CTAs l, l + 32, ... in registers.
+            constexpr int UMAX = 8;  // G <= 256
+            u64 hk[UMAX];
+            int hp[UMAX];
+#pragma unroll
+            for (int u = 0; u < UMAX; ++u) {
+                const int g = lane + 32 * u;
+                hp[u] = 0;
+                hk[u] = g < G ? wkey[g * PUB] : kNoKey;
             }
+            auto local_min = [&](u64 &lm, int &lu) {
+                lm = hk[0];
+                lu = 0;
+#pragma unroll
+                for (int u = 1; u < UMAX; ++u) {
+                    if (hk[u] < lm) {
+                        lm = hk[u];
+                        lu = u;
+                    }
+                }
+            };
+            u64 lm;
+            int lu;
+            local_min(lm, lu);
             int np = 0;
             int member = -1;  // lane 2a holds i_a, lane 2a + 1 holds j_a
             unsigned front = 0;  // value bits of the last entry visited
@@ -911,21 +917,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 const int src = __ffs(__ballot_sync(kFull, lm == m)) - 1;
                 unsigned col = 0;
                 if (lane == src) {
-                    const int h = hd[lg];
-                    col = wcol[lg * PUB + h];
-                    hd[lg] = h + 1;
-                    lm = kNoKey;
-                    lg = -1;
-                    for (int g = lane; g < G; g += 32) {
-                        const int hh = hd[g];
-                        if (hh < PUB) {
-                            const u64 kk = wkey[g * PUB + hh];
-                            if (kk < lm) {
-                                lm = kk;
-                                lg = g;
-                            }
+#pragma unroll
+                    for (int u = 0; u < UMAX; ++u) {
+                        if (u == lu) {
+                            const int g = lane + 32 * u;
+                            col = wcol[g * PUB + hp[u]];
+                            hp[u] += 1;
+                            hk[u] = hp[u] < PUB ? wkey[g * PUB + hp[u]] : kNoKey;
                         }
                     }
+                    local_min(lm, lu);
                 }
                 col = __shfl_sync(kFull, col, src);
                 const int row = (int)(((unsigned)m) >> 3);
@@ -1063,27 +1064,22 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (owner_of(m) == b)
                 mflag[slot_of(m)] = 1;
         }
-        for (int e = tid; e < 4 * s * s; e += NT) {
-            const int u = e / (2 * s), v = e % (2 * s);
-            if (u < v && (u >> 1) != (v >> 1)) {
+        // the cells between members of different pairs: loaded now, landed in
+        // shared memory after pass 1 (member u = 2a + (0 for i_a, 1 for j_a))
+        constexpr int DMR = (4 * S * S + NT - 1) / NT;
+        float dmv[DMR];
+#pragma unroll
+        for (int q = 0; q < DMR; ++q) {
+            const int e = tid + q * NT;
+            const int u = e / (2 * S), v = e % (2 * S);
+            dmv[q] = 0.0f;
+            if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
                 const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                 const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                const float d = __ldcg(p.D + cell_at(p, mu, mv));
-                sh.Dm[u][v] = d;
-                sh.Dm[v][u] = d;
+                dmv[q] = __ldcg(p.D + cell_at(p, mu, mv));
             }
         }
         __syncthreads();
-        // cells (i_a, i_b) and (i_a, j_b) after merge a alone
-        for (int e = tid; e < s * s; e += NT) {
-            const int a = e / s, c = e % s;
-            if (a != c) {
-                sh.X[a][c] = lw_cell(p.linkage, sh.Dm[2 * c][2 * a], sh.Dm[2 * c][2 * a + 1], sh.ph[a],
-                                     sh.szi[a], sh.szj[a], sh.szi[c]);
-                sh.Y[a][c] = lw_cell(p.linkage, sh.Dm[2 * c + 1][2 * a], sh.Dm[2 * c + 1][2 * a + 1],
-                                     sh.ph[a], sh.szi[a], sh.szj[a], sh.szj[c]);
-            }
-        }
         lap(ph1);
 
         // ---- pass 1: new cells of every live k outside the chain (reads only);
@@ -1146,14 +1142,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     kok = ok;
             }
         }
-        __syncthreads();
-        // cell (i_a, i_b) after merge a and then merge b
-        for (int e = tid; e < s * s; e += NT) {
-            const int a = e / s, c = e % s;
-            if (a < c)
-                sh.C[a][c] = lw_cell(p.linkage, sh.X[a][c], sh.Y[a][c], sh.ph[c], sh.szi[c], sh.szj[c],
-                                     sh.szi[a] + sh.szj[a]);
+#pragma unroll
+        for (int q = 0; q < DMR; ++q) {
+            const int e = tid + q * NT;
+            const int u = e / (2 * S), v = e % (2 * S);
+            if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
+                sh.Dm[u][v] = dmv[q];
+                sh.Dm[v][u] = dmv[q];
+            }
         }
+        __syncthreads();
         if (tid < 2 * S)
             __stcg(p.recB + (size_t)b * 2 * S + tid, tid < S ? sh.amin[tid] : sh.hmin[tid - S]);
         lap(ph2);
@@ -1164,6 +1162,24 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         // the K smallest keys of the row over live columns.  Nobody rewrites a
         // cell before the barrier except the cells of this round's merges,
         // which the install replays.
+        // cells (i_a, i_b) and (i_a, j_b) after merge a alone, then (i_a, i_b)
+        // after merges a and b: read only after barrier B
+        for (int e = tid; e < s * s; e += NT) {
+            const int a = e / s, c = e % s;
+            if (a != c) {
+                sh.X[a][c] = lw_cell(p.linkage, sh.Dm[2 * c][2 * a], sh.Dm[2 * c][2 * a + 1], sh.ph[a],
+                                     sh.szi[a], sh.szj[a], sh.szi[c]);
+                sh.Y[a][c] = lw_cell(p.linkage, sh.Dm[2 * c + 1][2 * a], sh.Dm[2 * c + 1][2 * a + 1],
+                                     sh.ph[a], sh.szi[a], sh.szj[a], sh.szj[c]);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < s * s; e += NT) {
+            const int a = e / s, c = e % s;
+            if (a < c)
+                sh.C[a][c] = lw_cell(p.linkage, sh.X[a][c], sh.Y[a][c], sh.ph[c], sh.szi[c], sh.szj[c],
+                                     sh.szi[a] + sh.szj[a]);
+        }
         {
             const int nexec = sh.nexec;
             for (int s2 = b; s2 < nexec; s2 += G) {
@@ -1657,10 +1673,10 @@ size_t merge_smem_bytes(long long n, int G)
     const long long nb = (n + kRowBlock - 1) / kRowBlock;
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
-    // bitmap; published entries (keys, column words, walk positions); per
+    // bitmap; published entries (keys, column words); per
     // slot: K keys, bound, size, count, refill round and position, chain flag
     const long long pub = G == 1 ? kPubOne : kPub;
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + (((long long)G * 4 + 15) & ~15LL) +
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 +
                     Rmax * (8 * K + 8 + 4 * 5 + 1));
 }
 
