@@ -50,8 +50,8 @@ FALLBACK_HBM_GBS = 6800.0
 # source it was taken on and is reported only while that source is unchanged.
 MEASURED_TRAFFIC = {
     "workload": "conformer65536:1",
-    "kernel_sha256": "0662e81b37a359d91fed622c82b95213b4f0cf258d8e52a32439827e7a31d9b3",
-    "bytes_per_launch": 421.70e9 + 43.44e9,
+    "kernel_sha256": "2c83efffb5d96421fa362896826665275c162ce8ce80c34f1773b6978d3cbc55",
+    "bytes_per_launch": 419.66e9 + 35.04e9,
 }
 
 
