@@ -12,9 +12,10 @@ constexpr int kRowBlock = 32;            // rows per ownership block (one warp)
 constexpr int kCacheKeys = 4;            // smallest keys cached per row
 constexpr int kPub = 4;                  // entries a CTA of a multi-CTA grid publishes per round
 constexpr int kPubOne = 16;              // entries a job's only CTA publishes per round
-constexpr int kRound = 16;               // most merges one round certifies
+constexpr int kRound = 32;               // most merges one round of a multi-CTA grid certifies
+constexpr int kRoundOne = 16;            // the same for a job's only CTA
 constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
-constexpr int kMaxReq = 128;             // refill requests served per round
+constexpr int kMaxReq = 256;             // refill requests served per round
 constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
 constexpr int kStats = 16;
 constexpr uint64_t kNoKey = ~0ull;
@@ -126,8 +127,9 @@ struct BatchParams {
 // infinite or negative cell sets *status to kErrInput.
 cudaError_t launch_expand(const float *packed, float *full, long long n, int *status, cudaStream_t stream);
 
-// Bytes of dynamic shared memory the merge kernel needs for (n, G).
-size_t merge_smem_bytes(long long n, int G);
+// Bytes of dynamic shared memory the merge kernel needs for (n, G) with CTAs
+// of nt threads.
+size_t merge_smem_bytes(long long n, int G, int nt);
 // CTA sizes the kernels are built for: 128, 256 or 512 threads (4, 2 or 1
 // CTAs per SM by registers).
 // True if a grid of G CTAs of nt threads for n objects fits co-resident on

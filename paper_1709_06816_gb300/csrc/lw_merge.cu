@@ -216,12 +216,15 @@ __device__ __forceinline__ void cand_min(Cand &x, const Cand &y)
         x = y;
 }
 
-constexpr int S = kRound;
+// Most merges one round certifies: a one-CTA job publishes kPubOne entries
+// and walks at most kRoundOne pairs; a grid walks up to kRound.
+__host__ __device__ constexpr int round_of(int pub) { return pub == kPubOne ? kRoundOne : kRound; }
 constexpr unsigned kFull = 0xffffffffu;
 constexpr u64 kHi = 0xffffffff00000000ull;
 static_assert(kPub <= kPubOne && kPub % 4 == 0 && kPubOne % 4 == 0, "record layout");
 static_assert(K == 4, "sort_list is a 4-input network");
-static_assert(S == 16, "certification and pair minima use groups of 16 lanes");
+static_assert(kRound <= 32 && (32 % kRound) == 0 && (32 % kRoundOne) == 0,
+              "certification and pair minima use lane groups of the round size");
 
 // Sort a K-list in which any entries were replaced by kNoKey.
 __device__ __forceinline__ void sort_list(u64 (&L)[K])
@@ -270,7 +273,7 @@ __device__ __forceinline__ Cand cell_cand(unsigned vb, unsigned x, unsigned y)
     return c;
 }
 
-template <int NT>
+template <int NT, int S>
 struct Shared {
     static constexpr int W = NT / 32;
     u64 tk[W][kPubOne];
@@ -308,8 +311,8 @@ struct Shared {
 // kMaxReq.  Thread t holds CTA t's request count and rows.  Sets
 // sh.exec_row and sh.nexec; thread b gives this CTA's own requests (list
 // pq) their list positions.
-template <int NT>
-__device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT> &sh, int pq,
+template <int NT, int S>
+__device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, Shared<NT, S> &sh, int pq,
                                   int *pend_t, int *pend_s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -354,8 +357,8 @@ __device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, S
 }
 
 // KK smallest keys over every thread's sorted list; result in sh.tko (all threads).
-template <int NT, int KK>
-__device__ void block_topk(u64 (&L)[KK], Shared<NT> &sh)
+template <int NT, int S, int KK>
+__device__ void block_topk(u64 (&L)[KK], Shared<NT, S> &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u64 w[KK];
@@ -397,8 +400,8 @@ __device__ __forceinline__ void grid_arrive(const MergeParams &p, unsigned &epoc
     }
 }
 
-template <int NT>
-__device__ bool grid_wait(const MergeParams &p, unsigned epoch, Shared<NT> &sh)
+template <int NT, int S>
+__device__ bool grid_wait(const MergeParams &p, unsigned epoch, Shared<NT, S> &sh)
 {
     if (threadIdx.x == 0) {
         int st = 0;
@@ -505,8 +508,8 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
 // K smallest keys of row r over live columns, computed by the whole CTA (a
 // refill, or a row whose cache emptied).  Adds the live cells read to
 // `live_cells`.  Result in sh.tko.
-template <int NT>
-__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT> &sh,
+template <int NT, int S>
+__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT, S> &sh,
                                long long &live_cells)
 {
     const long long n = p.n;
@@ -620,8 +623,10 @@ __device__ void warp_row_refresh(const MergeParams &p, long long r, const unsign
 // of the job calls this with the same p).  smem_raw: merge_smem_bytes(n, G)
 // bytes of dynamic shared memory.
 template <int NT, int PUB>
-__device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw, Shared<NT> &sh)
+__device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem_raw,
+                          Shared<NT, round_of(PUB)> &sh)
 {
+    constexpr int S = round_of(PUB);
     constexpr int W = NT / 32;
     const long long n = p.n;
     const int G = p.G;
@@ -649,6 +654,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     q0 += (size_t)Rmax * 8;
     unsigned *wcol = reinterpret_cast<unsigned *>(q0);
     q0 += (size_t)G * PUB * 4;
+    float *kvs = reinterpret_cast<float *>(q0);  // [S][NT]: pass-1 values of each thread's first row
+    q0 += (size_t)S * NT * 4;
     int *rsize = reinterpret_cast<int *>(q0);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
@@ -906,7 +913,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             int lu;
             local_min(lm, lu);
             int np = 0;
-            int member = -1;  // lane 2a holds i_a, lane 2a + 1 holds j_a
+            // member 2a = i_a, 2a + 1 = j_a: lane l holds members l and l + 32
+            int member0 = -1, member1 = -1;
             unsigned front = 0;  // value bits of the last entry visited
             for (int guard = 0; guard <= G * PUB; ++guard) {
                 const u64 m = warp_u64_min(lm);
@@ -931,16 +939,23 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 col = __shfl_sync(kFull, col, src);
                 const int row = (int)(((unsigned)m) >> 3);
                 bool stop = (col & kHardStop) != 0;
-                if (!__any_sync(kFull, member == row)) {
+                if (!__any_sync(kFull, member0 == row || member1 == row)) {
                     if (col & kRowStop) {
                         stop = true;  // the row's smallest untouched cell is unknown
                     } else {
                         const int c = (int)(col & kColMask);
-                        if (!__any_sync(kFull, member == c)) {
-                            if (lane == 2 * np)
-                                member = row;
-                            if (lane == 2 * np + 1)
-                                member = c;
+                        if (!__any_sync(kFull, member0 == c || member1 == c)) {
+                            if (2 * np < 32) {
+                                if (lane == 2 * np)
+                                    member0 = row;
+                                if (lane == 2 * np + 1)
+                                    member0 = c;
+                            } else {
+                                if (lane == 2 * np - 32)
+                                    member1 = row;
+                                if (lane == 2 * np - 31)
+                                    member1 = c;
+                            }
                             if (lane == 0) {
                                 sh.pi[np] = row;
                                 sh.pj[np] = c;
@@ -1066,29 +1081,43 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         // the cells between members of different pairs: loaded now, landed in
         // shared memory after pass 1 (member u = 2a + (0 for i_a, 1 for j_a))
-        constexpr int DMR = (4 * S * S + NT - 1) / NT;
+        // (more than eight per thread go to shared memory at once)
+        constexpr int DMALL = (4 * S * S + NT - 1) / NT;
+        constexpr bool DM_REG = DMALL <= 8;
+        constexpr int DMR = DM_REG ? DMALL : 1;
         float dmv[DMR];
+        if (DM_REG) {
 #pragma unroll
-        for (int q = 0; q < DMR; ++q) {
-            const int e = tid + q * NT;
-            const int u = e / (2 * S), v = e % (2 * S);
-            dmv[q] = 0.0f;
-            if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
-                const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
-                const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                dmv[q] = __ldcg(p.D + cell_at(p, mu, mv));
+            for (int q = 0; q < DMR; ++q) {
+                const int e = tid + q * NT;
+                const int u = e / (2 * S), v = e % (2 * S);
+                dmv[q] = 0.0f;
+                if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
+                    const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
+                    const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
+                    dmv[q] = __ldcg(p.D + cell_at(p, mu, mv));
+                }
+            }
+        } else {
+            for (int e = tid; e < 4 * S * S; e += NT) {
+                const int u = e / (2 * S), v = e % (2 * S);
+                if (u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
+                    const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
+                    const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
+                    const float d = __ldcg(p.D + cell_at(p, mu, mv));
+                    sh.Dm[u][v] = d;
+                    sh.Dm[v][u] = d;
+                }
             }
         }
         __syncthreads();
         lap(ph1);
 
-        // ---- pass 1: new cells of every live k outside the chain (reads only);
-        // the values of each thread's first row stay in registers for pass 2
-        float kv[S];
+        // ---- pass 1: new cells of every live k outside the chain (reads only),
+        // the pairs in groups of 16; the values of each thread's first row are
+        // kept in shared memory for pass 2
+        constexpr int PG = 16;
         bool kok = false;
-#pragma unroll
-        for (int a = 0; a < S; ++a)
-            kv[a] = 0.0f;
         if (s > 0) {
             for (int l0 = 0; l0 < R; l0 += NT) {
                 const int l = l0 + tid;
@@ -1103,57 +1132,67 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
                 // cell (k, i): in the full matrix row i holds it (consecutive
                 // k of a warp read consecutive words); packed, row k for k < i
-                float va[S], vb[S];
                 const long long bk = row_base(p, k);
                 const bool full = p.full;
 #pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    va[a] = 0.0f;
-                    vb[a] = 0.0f;
-                    if (ok && a < s) {
-                        const long long i = sh.pi[a], j = sh.pj[a];
-                        va[a] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
-                        vb[a] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    if (a >= s)
+                for (int a0 = 0; a0 < S; a0 += PG) {
+                    if (a0 >= s)
                         break;
-                    u64 ka = kNoKey, kh = kNoKey;
-                    if (ok) {
-                        const float v = lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                        if (l0 == 0)
-                            kv[a] = v;
-                        ka = make_key(v, (unsigned)k);
-                        if (k > sh.pi[a])
-                            kh = ka;
+                    float va[PG], vb[PG];
+#pragma unroll
+                    for (int u = 0; u < PG; ++u) {
+                        const int a = a0 + u;
+                        va[u] = 0.0f;
+                        vb[u] = 0.0f;
+                        if (ok && a < s) {
+                            const long long i = sh.pi[a], j = sh.pj[a];
+                            va[u] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
+                            vb[u] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
+                        }
                     }
-                    const u64 ma = warp_u64_min(ka);
-                    const u64 mh = warp_u64_min(kh);
-                    if (lane == 0) {
-                        if (ma != kNoKey)
-                            atomicMin(&sh.amin[a], ma);
-                        if (mh != kNoKey)
-                            atomicMin(&sh.hmin[a], mh);
+#pragma unroll
+                    for (int u = 0; u < PG; ++u) {
+                        const int a = a0 + u;
+                        if (a >= s)
+                            break;
+                        u64 ka = kNoKey, kh = kNoKey;
+                        if (ok) {
+                            const float v = lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                            if (l0 == 0)
+                                kvs[a * NT + tid] = v;
+                            ka = make_key(v, (unsigned)k);
+                            if (k > sh.pi[a])
+                                kh = ka;
+                        }
+                        const u64 ma = warp_u64_min(ka);
+                        const u64 mh = warp_u64_min(kh);
+                        if (lane == 0) {
+                            if (ma != kNoKey)
+                                atomicMin(&sh.amin[a], ma);
+                            if (mh != kNoKey)
+                                atomicMin(&sh.hmin[a], mh);
+                        }
                     }
                 }
                 if (l0 == 0)
                     kok = ok;
             }
         }
+        if (DM_REG) {
 #pragma unroll
-        for (int q = 0; q < DMR; ++q) {
-            const int e = tid + q * NT;
-            const int u = e / (2 * S), v = e % (2 * S);
-            if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
-                sh.Dm[u][v] = dmv[q];
-                sh.Dm[v][u] = dmv[q];
+            for (int q = 0; q < DMR; ++q) {
+                const int e = tid + q * NT;
+                const int u = e / (2 * S), v = e % (2 * S);
+                if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
+                    sh.Dm[u][v] = dmv[q];
+                    sh.Dm[v][u] = dmv[q];
+                }
             }
         }
         __syncthreads();
         if (tid < 2 * S)
-            __stcg(p.recB + (size_t)b * 2 * S + tid, tid < S ? sh.amin[tid] : sh.hmin[tid - S]);
+            __stcg(p.recB + (size_t)b * 2 * kRound + (tid < S ? tid : kRound + tid - S),
+                   tid < S ? sh.amin[tid] : sh.hmin[tid - S]);
         lap(ph2);
         grid_arrive(p, epoch);
 
@@ -1205,8 +1244,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             u64 ma = kNoKey, mh = kNoKey;
             if (a < s) {
                 for (int g = tid / S; g < G; g += NT / S) {
-                    const u64 x = __ldcg(p.recB + (size_t)g * 2 * S + a);
-                    const u64 y = __ldcg(p.recB + (size_t)g * 2 * S + S + a);
+                    const u64 x = __ldcg(p.recB + (size_t)g * 2 * kRound + a);
+                    const u64 y = __ldcg(p.recB + (size_t)g * 2 * kRound + kRound + a);
                     ma = x < ma ? x : ma;
                     mh = y < mh ? y : mh;
                 }
@@ -1227,10 +1266,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         __syncthreads();
         // certification: thread (p, a) takes the smallest cell that merge a
-        // (a < p) rewrote as seen after merge p - 1; the 16 threads of p reduce
+        // (a < p) rewrote as seen after merge p - 1; the S threads of p reduce
         // and compare with P_p
-        for (int e = tid; e < 16 * S; e += NT) {
-            const int pp = e >> 4, a = e & 15;
+        for (int e = tid; e < S * S; e += NT) {
+            const int pp = e / S, a = e % S;
             Cand M = {kNoKey, 0xffffffffu};
             if (pp >= 1 && pp < s && a < pp) {
                 const unsigned ia = (unsigned)sh.pi[a];
@@ -1245,7 +1284,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     cand_min(M, cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]));
             }
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
+            for (int o = S / 2; o > 0; o >>= 1) {
                 Cand y;
                 y.A = __shfl_xor_sync(kFull, M.A, o);
                 y.c = __shfl_xor_sync(kFull, M.c, o);
@@ -1399,55 +1438,62 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 const bool have = l0 == 0 && kok;
                 const long long bk = row_base(p, k);
                 const bool full = p.full;
-                float va[S], vb[S];
-#pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    va[a] = 0.0f;
-                    vb[a] = 0.0f;
-                    if (!have && a < L) {
-                        const long long i = sh.pi[a], j = sh.pj[a];
-                        va[a] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
-                        vb[a] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
-                    }
-                }
                 u64 Cc[K];
                 cache_load(Cc, l);
                 int c = ccnt[l];
                 u64 B = cB[l];
 #pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    if (a >= L)
+                for (int a0 = 0; a0 < S; a0 += PG) {
+                    if (a0 >= L)
                         break;
-                    const long long ia = sh.pi[a], ja = sh.pj[a];
-                    const float v =
-                        have ? kv[a] : lw_cell(p.linkage, va[a], vb[a], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                    __stcg(p.D + (full || k > ia ? sh.bi[a] + k : bk + ia), v);
-                    if (full)
-                        __stcg(p.D + bk + ia, v);  // the copy in row k
-                    ++st_updates;
-                    if (k < ja) {
-                        // row k loses column j; if k < i its cell (k, i) changed as well
-                        bool drop = false;
+                    float va[PG], vb[PG];
 #pragma unroll
-                        for (int q = 0; q < K; ++q) {
-                            const long long col = (long long)(unsigned)Cc[q];
-                            if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia))) {
-                                Cc[q] = kNoKey;
-                                drop = true;
+                    for (int u = 0; u < PG; ++u) {
+                        const int a = a0 + u;
+                        va[u] = 0.0f;
+                        vb[u] = 0.0f;
+                        if (!have && a < L) {
+                            const long long i = sh.pi[a], j = sh.pj[a];
+                            va[u] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
+                            vb[u] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < PG; ++u) {
+                        const int a = a0 + u;
+                        if (a >= L)
+                            break;
+                        const long long ia = sh.pi[a], ja = sh.pj[a];
+                        const float v = have ? kvs[a * NT + tid]
+                                             : lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                        __stcg(p.D + (full || k > ia ? sh.bi[a] + k : bk + ia), v);
+                        if (full)
+                            __stcg(p.D + bk + ia, v);  // the copy in row k
+                        ++st_updates;
+                        if (k < ja) {
+                            // row k loses column j; if k < i its cell (k, i) changed as well
+                            bool drop = false;
+#pragma unroll
+                            for (int q = 0; q < K; ++q) {
+                                const long long col = (long long)(unsigned)Cc[q];
+                                if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia))) {
+                                    Cc[q] = kNoKey;
+                                    drop = true;
+                                }
                             }
-                        }
-                        if (drop) {
-                            close_holes(Cc);
-                            c = list_count(Cc);
-                        }
-                        if (k < ia) {
-                            const u64 x = make_key(v, (unsigned)ia);
-                            if (x <= B) {
-                                list_insert(Cc, x);
-                                if (c == K)
-                                    B = Cc[K - 1];
-                                else
-                                    ++c;
+                            if (drop) {
+                                close_holes(Cc);
+                                c = list_count(Cc);
+                            }
+                            if (k < ia) {
+                                const u64 x = make_key(v, (unsigned)ia);
+                                if (x <= B) {
+                                    list_insert(Cc, x);
+                                    if (c == K)
+                                        B = Cc[K - 1];
+                                    else
+                                        ++c;
+                                }
                             }
                         }
                     }
@@ -1565,7 +1611,7 @@ template <int NT, int MINB, int PUB>
 __global__ void __launch_bounds__(NT, MINB) merge_kernel(MergeParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared<NT> sh;
+    __shared__ Shared<NT, round_of(PUB)> sh;
     merge_job<NT, PUB>(p, blockIdx.x, smem_raw, sh);
 }
 
@@ -1577,7 +1623,7 @@ template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared<NT> sh;
+    __shared__ Shared<NT, kRoundOne> sh;
     __shared__ int job;
     const WorkspaceLayout L = workspace_layout(bp.n_max, 1);
     char *ws = bp.ws + (size_t)blockIdx.x * L.total;
@@ -1668,16 +1714,18 @@ cudaError_t launch_expand(const float *packed, float *full, long long n, int *st
     return cudaGetLastError();
 }
 
-size_t merge_smem_bytes(long long n, int G)
+size_t merge_smem_bytes(long long n, int G, int nt)
 {
     const long long nb = (n + kRowBlock - 1) / kRowBlock;
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
     // bitmap; published entries (keys, column words); per
-    // slot: K keys, bound, size, count, refill round and position, chain flag
+    // slot: K keys, bound, size, count, refill round and position, chain
+    // flag; pass-1 values of each thread's first row (one float per pair)
     const long long pub = G == 1 ? kPubOne : kPub;
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 +
-                    Rmax * (8 * K + 8 + 4 * 5 + 1));
+    const long long S = round_of((int)pub);
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + S * nt * 4 +
+                    ((Rmax * (8 * K + 8 + 4 * 5 + 1) + 15) & ~15LL));
 }
 
 namespace {
@@ -1709,22 +1757,29 @@ const void *batch_fn(int nt)
     }
 }
 
-size_t static_smem(int nt)
+size_t static_smem(int nt, int G)
 {
+    if (G == 1) {
+        switch (nt) {
+        case 128: return sizeof(Shared<128, kRoundOne>);
+        case 256: return sizeof(Shared<256, kRoundOne>);
+        default: return sizeof(Shared<512, kRoundOne>);
+        }
+    }
     switch (nt) {
-    case 128: return sizeof(Shared<128>);
-    case 256: return sizeof(Shared<256>);
-    default: return sizeof(Shared<512>);
+    case 128: return sizeof(Shared<128, kRound>);
+    case 256: return sizeof(Shared<256, kRound>);
+    default: return sizeof(Shared<512, kRound>);
     }
 }
 
-int fit_per_sm(const void *fn, int nt, size_t smem)
+int fit_per_sm(const void *fn, int nt, int G, size_t smem)
 {
     int dev = 0, limit = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return 0;
-    if (smem + static_smem(nt) > (size_t)limit)
+    if (smem + static_smem(nt, G) > (size_t)limit)
         return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -1742,19 +1797,19 @@ bool merge_config_ok(long long n, int G, int num_sms, int nt)
     // the first G threads read the CTAs' records
     if (G < 1 || G > num_sms || G > nt)
         return false;
-    return fit_per_sm(merge_fn(nt, G), nt, merge_smem_bytes(n, G)) >= 1;
+    return fit_per_sm(merge_fn(nt, G), nt, G, merge_smem_bytes(n, G, nt)) >= 1;
 }
 
 int batch_ctas_per_sm(long long n_max, int nt)
 {
-    return fit_per_sm(batch_fn(nt), nt, merge_smem_bytes(n_max, 1));
+    return fit_per_sm(batch_fn(nt), nt, 1, merge_smem_bytes(n_max, 1, nt));
 }
 
 cudaError_t launch_batch(const BatchParams &bp, int grid, int nt, cudaStream_t stream)
 {
     // batch_ctas_per_sm(bp.n_max, nt) has set the kernel's shared-memory limit
     // (this launch may be recorded into a graph, where no attribute is set)
-    const size_t smem = merge_smem_bytes(bp.n_max, 1);
+    const size_t smem = merge_smem_bytes(bp.n_max, 1, nt);
     BatchParams q = bp;
     void *args[] = {&q};
     return cudaLaunchKernel(batch_fn(nt), dim3(grid), dim3(nt), args, smem, stream);
@@ -1762,7 +1817,7 @@ cudaError_t launch_batch(const BatchParams &bp, int grid, int nt, cudaStream_t s
 
 cudaError_t launch_merge(const MergeParams &p, int nt, cudaStream_t stream)
 {
-    const size_t smem = merge_smem_bytes(p.n, p.G);
+    const size_t smem = merge_smem_bytes(p.n, p.G, nt);
     const void *fn = merge_fn(nt, p.G);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
