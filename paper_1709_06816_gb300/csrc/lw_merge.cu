@@ -655,7 +655,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     unsigned *wcol = reinterpret_cast<unsigned *>(q0);
     q0 += (size_t)G * PUB * 4;
     float *kvs = reinterpret_cast<float *>(q0);  // [S][NT]: pass-1 values of each thread's first row
-    q0 += (size_t)S * NT * 4;
+    q0 += S > 16 ? (size_t)S * NT * 4 : 0;       // (up to 16 pairs they stay in registers)
     int *rsize = reinterpret_cast<int *>(q0);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
@@ -1117,6 +1117,12 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         // the pairs in groups of 16; the values of each thread's first row are
         // kept in shared memory for pass 2
         constexpr int PG = 16;
+        // up to 16 pairs the values stay in registers; more go to shared memory
+        constexpr bool KV_REG = S <= PG;
+        float kv[KV_REG ? S : 1];
+#pragma unroll
+        for (int a = 0; a < (KV_REG ? S : 1); ++a)
+            kv[a] = 0.0f;
         bool kok = false;
         if (s > 0) {
             for (int l0 = 0; l0 < R; l0 += NT) {
@@ -1158,14 +1164,27 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         u64 ka = kNoKey, kh = kNoKey;
                         if (ok) {
                             const float v = lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                            if (l0 == 0)
-                                kvs[a * NT + tid] = v;
+                            if (l0 == 0) {
+                                if (KV_REG)
+                                    kv[KV_REG ? a : 0] = v;
+                                else
+                                    kvs[a * NT + tid] = v;
+                            }
                             ka = make_key(v, (unsigned)k);
                             if (k > sh.pi[a])
                                 kh = ka;
                         }
+                        // a warp's rows are one block of 32 consecutive k: unless the
+                        // block holds i_a, "k > i_a" is all of it or none of it
+                        const long long k0 = (long long)(b + (long long)G * (l >> 5)) * kRowBlock;
                         const u64 ma = warp_u64_min(ka);
-                        const u64 mh = warp_u64_min(kh);
+                        u64 mh;
+                        if (k0 > sh.pi[a])
+                            mh = ma;
+                        else if (k0 + kRowBlock <= sh.pi[a])
+                            mh = kNoKey;
+                        else
+                            mh = warp_u64_min(kh);
                         if (lane == 0) {
                             if (ma != kNoKey)
                                 atomicMin(&sh.amin[a], ma);
@@ -1464,7 +1483,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         if (a >= L)
                             break;
                         const long long ia = sh.pi[a], ja = sh.pj[a];
-                        const float v = have ? kvs[a * NT + tid]
+                        const float v = have ? (KV_REG ? kv[KV_REG ? a : 0] : kvs[a * NT + tid])
                                              : lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
                         __stcg(p.D + (full || k > ia ? sh.bi[a] + k : bk + ia), v);
                         if (full)
@@ -1724,7 +1743,7 @@ size_t merge_smem_bytes(long long n, int G, int nt)
     // flag; pass-1 values of each thread's first row (one float per pair)
     const long long pub = G == 1 ? kPubOne : kPub;
     const long long S = round_of((int)pub);
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + S * nt * 4 +
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + (S > 16 ? S * nt * 4 : 0) +
                     ((Rmax * (8 * K + 8 + 4 * 5 + 1) + 15) & ~15LL));
 }
 
