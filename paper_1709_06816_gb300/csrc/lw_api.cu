@@ -36,6 +36,11 @@ struct lw_ctx {
     size_t dbuf_cap = 0;
     void *full = nullptr;   // symmetric n x n working matrix (multi-CTA runs)
     size_t full_cap = 0;
+    // side streams for uploading a host matrix in parallel pieces
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t copy_stream[kCopyStreams] = {};
+    cudaEvent_t copy_fork = nullptr;
+    cudaEvent_t copy_join[kCopyStreams] = {};
     void *obuf = nullptr;   // device outputs for host output pointers
     size_t obuf_cap = 0;
     int *h_status = nullptr;       // pinned [4]
@@ -103,6 +108,46 @@ lw_status ensure(lw_ctx *ctx, void **buf, size_t *cap, size_t need, const char *
     }
     *cap = need;
     return LW_OK;
+}
+
+// Host-to-device copy of a large host matrix on the context's stream: pieces
+// of 1 GiB dealt to side streams, so that several copy engines work at once;
+// the context's stream waits for all of them.  One cudaMemcpyAsync per piece.
+cudaError_t upload(lw_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    constexpr size_t kPiece = size_t(1) << 30;
+    if (bytes <= kPiece)
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e;
+    if (!ctx->copy_fork) {
+        if ((e = cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+        for (int q = 0; q < lw_ctx::kCopyStreams; ++q) {
+            if ((e = cudaStreamCreateWithFlags(&ctx->copy_stream[q], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&ctx->copy_join[q], cudaEventDisableTiming)) != cudaSuccess)
+                return e;
+        }
+    }
+    if ((e = cudaEventRecord(ctx->copy_fork, ctx->stream)) != cudaSuccess)
+        return e;
+    for (int q = 0; q < lw_ctx::kCopyStreams; ++q)
+        if ((e = cudaStreamWaitEvent(ctx->copy_stream[q], ctx->copy_fork, 0)) != cudaSuccess)
+            return e;
+    const char *s8 = static_cast<const char *>(src);
+    char *d8 = static_cast<char *>(dst);
+    int q = 0;
+    for (size_t off = 0; off < bytes; off += kPiece, q = (q + 1) % lw_ctx::kCopyStreams) {
+        const size_t len = bytes - off < kPiece ? bytes - off : kPiece;
+        if ((e = cudaMemcpyAsync(d8 + off, s8 + off, len, cudaMemcpyHostToDevice, ctx->copy_stream[q])) !=
+            cudaSuccess)
+            return e;
+    }
+    for (int k = 0; k < lw_ctx::kCopyStreams; ++k) {
+        if ((e = cudaEventRecord(ctx->copy_join[k], ctx->copy_stream[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->stream, ctx->copy_join[k], 0)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 struct BusyGuard {
@@ -333,9 +378,8 @@ lw_status lw_cluster(lw_ctx *ctx, float *dist, int64_t n, int linkage, int32_t *
         s = ensure(ctx, (void **)&ctx->dbuf, &ctx->dbuf_cap, cells * sizeof(float), "matrix copy");
         if (s != LW_OK)
             return s;
-        if ((e = cudaMemcpyAsync(ctx->dbuf, dist, cells * sizeof(float), cudaMemcpyHostToDevice,
-                                 ctx->stream)) != cudaSuccess)
-            return cuda_fail(ctx, e, "cudaMemcpyAsync(matrix)");
+        if ((e = upload(ctx, ctx->dbuf, dist, cells * sizeof(float))) != cudaSuccess)
+            return cuda_fail(ctx, e, "matrix upload");
         ddist = ctx->dbuf;
     }
     const bool dev_m = is_device_ptr(merges_out), dev_h = is_device_ptr(heights_out);
@@ -840,6 +884,14 @@ void lw_destroy(lw_ctx *ctx)
     cudaFree(ctx->obuf);
     cudaFreeHost(ctx->h_status);
     cudaFreeHost(ctx->h_stats);
+    for (int q = 0; q < lw_ctx::kCopyStreams; ++q) {
+        if (ctx->copy_stream[q])
+            cudaStreamDestroy(ctx->copy_stream[q]);
+        if (ctx->copy_join[q])
+            cudaEventDestroy(ctx->copy_join[q]);
+    }
+    if (ctx->copy_fork)
+        cudaEventDestroy(ctx->copy_fork);
     if (ctx->own_stream && ctx->stream)
         cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
