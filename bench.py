@@ -50,8 +50,8 @@ FALLBACK_HBM_GBS = 6800.0
 # source it was taken on and is reported only while that source is unchanged.
 MEASURED_TRAFFIC = {
     "workload": "conformer65536:1",
-    "kernel_sha256": "2c83efffb5d96421fa362896826665275c162ce8ce80c34f1773b6978d3cbc55",
-    "bytes_per_launch": 419.66e9 + 35.04e9,
+    "kernel_sha256": "096941a558908fbf3185be1ee45c495ccf3df4fd1267e67bdc6b445195425937",
+    "bytes_per_launch": 441.88e9 + 35.28e9,
 }
 
 
