@@ -14,7 +14,7 @@ constexpr int kPub = 4;                  // entries a CTA of a multi-CTA grid pu
 constexpr int kPubOne = 16;              // entries a job's only CTA publishes per round
 constexpr int kRound = 32;               // most merges one round of a multi-CTA grid certifies
 constexpr int kRoundOne = 16;            // the same for a job's only CTA
-constexpr int kRefillAt = 2;             // ask for a refill at this many keys or fewer
+constexpr int kRefillAt = 0;             // ask for a refill when the cache holds this many keys or fewer
 constexpr int kMaxReq = 256;             // refill requests served per round
 constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
 constexpr int kStats = 16;

@@ -12,9 +12,10 @@ on the host, one round at a time, with the kernel's data structures:
 * the walk over the union of the published lists, the chain of disjoint
   pairs, the new cells computed before anything is written, the certified
   prefix, the bookkeeping (survivor caches from the smallest new cell to the
-  right and the cells between chain members), and the refills (requested at
-  <= 2 keys, scanned one round later, installed the round after with the
-  merges in between replayed) or, for one CTA, the immediate refresh.
+  right and the cells between chain members), and the refills (requested when
+  a cache holds `refill_at` keys or fewer, scanned one round later, installed
+  the round after with the merges in between replayed) or, for one CTA, the
+  immediate refresh.
 
 It shares no code with the oracle or the library.  Tests compare its output
 with the oracle bit for bit, and a planted mistake (accepting the whole chain
@@ -26,7 +27,6 @@ from __future__ import annotations
 import numpy as np
 
 K = 4            # cached keys per row
-REFILL_AT = 2    # ask for a refill at this many keys or fewer
 MAX_REQ = 256    # refill rows served per round
 REQ_PER_CTA = 8
 NOKEY = (1 << 64) - 1
@@ -62,8 +62,9 @@ def lw_cell(linkage, dki, dkj, dij, ni, nj, nk):
 
 
 class RoundModel:
-    def __init__(self, packed, n, linkage, G=1, chain=16, pub=4, certify=True):
+    def __init__(self, packed, n, linkage, G=1, chain=16, pub=4, certify=True, refill_at=0):
         self.n, self.link, self.G = n, linkage, G
+        self.refill_at = refill_at
         self.chain = chain
         self.pub = pub
         self.certify = certify
@@ -252,7 +253,7 @@ class RoundModel:
                     ks = sorted(cands)[:K]
                     B = ks[K - 1] if len(cands) > K else NOKEY
                 self.cache[ia], self.bound[ia] = ks, B
-                if len(ks) <= REFILL_AT and B != NOKEY:
+                if len(ks) <= self.refill_at and B != NOKEY:
                     asked.append(ia)
             # pass 2: write the new cells, keep the caches
             for k in range(n):
@@ -277,9 +278,9 @@ class RoundModel:
                                     c += 1
                 self.cache[k], self.bound[k] = ks, B
                 if self.G == 1:
-                    if len(ks) <= REFILL_AT and B != NOKEY:
+                    if len(ks) <= self.refill_at and B != NOKEY:
                         refresh.append(k)
-                elif len(ks) <= REFILL_AT and B != NOKEY and k not in self.pend:
+                elif len(ks) <= self.refill_at and B != NOKEY and k not in self.pend:
                     asked.append(k)
             for a in range(L):
                 self.size[chain[a][0]] = szi[a] + szj[a]

@@ -19,12 +19,12 @@ CASES = [(n, kind) for n in (2, 5, 33, 70) for kind in ("gmm", "ties")]
 
 
 @pytest.mark.parametrize("link", range(4))
-@pytest.mark.parametrize("G,chain,pub", [(1, 16, 16), (3, 32, 4)])
-def test_model_matches_oracle(link, G, chain, pub):
+@pytest.mark.parametrize("G,chain,pub,refill_at", [(1, 16, 16, 0), (3, 32, 4, 0), (3, 32, 4, 2)])
+def test_model_matches_oracle(link, G, chain, pub, refill_at):
     for s, (n, kind) in enumerate(CASES):
         D = synth.small_gmm(n, 40 + s) if kind == "gmm" else synth.tie_heavy(n, 40 + s, levels=4)
         wm, wh, _, _ = oracle.cached(D.copy(), n, link)
-        m, h, rounds = RoundModel(D.copy(), n, link, G=G, chain=chain, pub=pub).run()
+        m, h, rounds = RoundModel(D.copy(), n, link, G=G, chain=chain, pub=pub, refill_at=refill_at).run()
         assert np.array_equal(m, wm), (n, kind)
         assert np.array_equal(_bits(h), _bits(wh)), (n, kind)
         assert rounds <= max(n - 1, 1) + 64  # rounds certify one merge or more, bar refill waits
