@@ -47,20 +47,28 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one merge
 # kernel launch on the bench workload, from one ncu capture
 # (profiles/merge_kernel_conformer65536_dram.md).  It describes the kernel
-# source it was taken on and is reported only while that source is unchanged.
+# sources it was taken on (lw_merge.cu and lw_internal.h) and is reported only
+# while they are unchanged.
 MEASURED_TRAFFIC = {
     "workload": "conformer65536:1",
-    "kernel_sha256": "096941a558908fbf3185be1ee45c495ccf3df4fd1267e67bdc6b445195425937",
-    "bytes_per_launch": 441.88e9 + 35.28e9,
+    "kernel_sha256": "7c0e5677cd92a7e49218651bb75f7ead4042337f7bf59c952b8328b019b096fa",
+    "bytes_per_launch": 366.76e9 + 35.06e9,
 }
 
 
-def measured_traffic(workload: str, linkage: int):
+def kernel_source_sha256() -> str:
+    """Hash of the merge kernel's sources (the kernel and its constants)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1709_06816_gb300", "csrc", "lw_merge.cu")
+    h = hashlib.sha256()
+    for name in ("lw_merge.cu", "lw_internal.h"):
+        with open(os.path.join(ROOT, "paper_1709_06816_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, linkage: int):
     try:
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = kernel_source_sha256()
     except OSError:
         return None
     if sha != MEASURED_TRAFFIC["kernel_sha256"] or f"{workload}:{linkage}" != MEASURED_TRAFFIC["workload"]:
