@@ -144,7 +144,7 @@ struct lw_server {
         }
     }
 
-    // One CTA for up to 2048 objects (256 threads up to 1024 objects, so that
+    // One CTA for up to 2048 objects (256 threads up to 512 objects, so that
     // two small requests share an SM, else 512 -- the batch autotuner's
     // finding on GB300); above that, 512-thread CTAs, one per 1024 objects.
     int grid_for(int64_t n) const
@@ -155,7 +155,7 @@ struct lw_server {
         return std::min(G, num_sms);
     }
 
-    static int threads_for(int64_t n) { return n <= 1024 ? 256 : 512; }
+    static int threads_for(int64_t n) { return n <= 512 ? 256 : 512; }
 
     // Launch request r on lane L (scheduler thread, mutex held).
     lw_status launch(Lane &L, const Request &r, size_t off)
