@@ -15,6 +15,7 @@ constexpr int kPubOne = 16;              // entries a job's only CTA publishes p
 constexpr int kRound = 32;               // most merges one round of a multi-CTA grid certifies
 constexpr int kRoundOne = 16;            // the same for a job's only CTA
 constexpr int kRefillAt = 0;             // ask for a refill when the cache holds this many keys or fewer
+constexpr int kSurvivorRefillAt = 1;     // the same for a survivor row right after its merge
 constexpr int kMaxReq = 256;             // refill requests served per round
 constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
 constexpr int kStats = 16;

@@ -1426,7 +1426,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 cB[l] = B;
                 rsize[l] = sh.szi[a] + sh.szj[a];
                 pend_t[l] = -1;
-                if (c <= kRefillAt && B != kNoKey)
+                // a survivor holds little more than its smallest cell: ask for
+                // its row now (other rows wait until their cache empties)
+                if (c <= kSurvivorRefillAt && B != kNoKey)
                     request(l, r);
             }
         }
