@@ -51,8 +51,8 @@ FALLBACK_HBM_GBS = 6800.0
 # while they are unchanged.
 MEASURED_TRAFFIC = {
     "workload": "conformer65536:1",
-    "kernel_sha256": "7c0e5677cd92a7e49218651bb75f7ead4042337f7bf59c952b8328b019b096fa",
-    "bytes_per_launch": 366.76e9 + 35.06e9,
+    "kernel_sha256": "81d4cbdac371a868e205a61181d1b73ef7e9f7d4404ac23dcaa52f3380bf35c2",
+    "bytes_per_launch": 370.64e9 + 35.09e9,
 }
 
 
