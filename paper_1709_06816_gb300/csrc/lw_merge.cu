@@ -18,18 +18,19 @@
 //
 // Rounds.  A grid barrier costs about a microsecond on GB300, more than the
 // arithmetic of one merge, so the kernel certifies several consecutive merges
-// of the sequential iteration per pair of barriers.  The merges are exactly
-// those of the step-by-step algorithm (same pairs, same order, same rounded
-// values); only the bookkeeping differs.  One round:
+// of the sequential iteration per pair of barriers (up to 32 for a grid, 16
+// for a job's only CTA).  The merges are exactly those of the step-by-step
+// algorithm (same pairs, same order, same rounded values); only the
+// bookkeeping differs.  One round:
 //
-//   A  every CTA publishes its kPub smallest cache entries, each row's
-//      entries followed by a stop mark at its bound B.  After the barrier
-//      every CTA walks the union of all published entries in (value, row,
-//      column) order and proposes a chain of disjoint pairs P_1..P_s: an
-//      entry whose row or column already belongs to a proposed pair is
-//      skipped, a stop mark of an untouched row (or the last entry of a CTA
-//      that had more) ends the walk.  P_{p+1} is then the smallest cell
-//      among those no earlier proposal touches.
+//   A  every CTA publishes its smallest cache entries (kPub of them, kPubOne
+//      for a job's only CTA), each row's entries followed by a stop mark at
+//      its bound B.  After the barrier every CTA walks the union of all
+//      published entries in (value, row, column) order and proposes a chain
+//      of disjoint pairs P_1..P_s: an entry whose row or column already
+//      belongs to a proposed pair is skipped, a stop mark of an untouched row
+//      (or the last entry of a CTA that had more) ends the walk.  P_{p+1} is
+//      then the smallest cell among those no earlier proposal touches.
 //   pass 1 (reads only): for every live k outside the chain and every pair a,
 //      the new distance D(k, i_a + j_a) of Section 4 step 3; each CTA
 //      publishes, per pair, its smallest new cell over all k and over k > i_a.
@@ -43,12 +44,14 @@
 //      kept (column j_a leaves, the new cell (k, i_a) enters when <= B), the
 //      survivor rows get their new caches from the published minima.
 //
-// A row whose cache runs low asks for a refill; in the window of the next
-// round's barrier B (after a CTA has arrived and before it waits) one warp of
-// every CTA scans that CTA's columns of the row and publishes a partial top-K
-// list; at the start of the round after that the owner merges the lists and
-// replays the merges of the round in between.  Rows scans stay off the
-// critical path.
+// Refills.  A row whose cache empties (a survivor row: right after its merge)
+// asks for a refill; in the window of the next round's barrier B (after a CTA
+// has arrived and before it waits) one CTA scans the whole row, all threads,
+// and publishes its top-K; at the start of the round after that the owner
+// takes the list and replays the merges of the round in between.  A row that
+// empties while its bound sits at the front of the merges is rescanned at
+// once by its owner.  A job's only CTA sees every write after pass 2 and
+// refreshes survivor and emptied rows itself, a warp per row.
 //
 // Exact arithmetic: every product and sum of the update uses __fmul_rn /
 // __fadd_rn / __fsub_rn (never contracted into FMA), the coefficient
