@@ -24,6 +24,9 @@
  *     Ward: T = n_i+n_j+n_k, a_i = fl((n_i+n_k)/T), a_j = fl((n_j+n_k)/T),
  *     b = -fl(n_k/T), g = 0; single: (0.5, 0.5, 0, -0.5);
  *     complete: (0.5, 0.5, 0, 0.5) (the form of Section 5.3 step 6);
+ *     weighted average: (0.5, 0.5, 0, 0); centroid: a_i, a_j as group
+ *     average, b = -fl(float(n_i n_j) / float((n_i+n_j)^2)), the integers
+ *     exact, each converted once;
  *   - the minimum is the smallest (value, i, j) in lexicographic order, so
  *     equal distances go to the lowest row i, then the lowest column j.
  *
@@ -50,7 +53,10 @@ typedef enum {
     LW_SINGLE = 0,   /* a_i = a_j = 1/2, b = 0, g = -1/2 */
     LW_COMPLETE = 1, /* a_i = a_j = 1/2, b = 0, g = +1/2 */
     LW_AVERAGE = 2,  /* a_i = n_i/(n_i+n_j), a_j = n_j/(n_i+n_j), b = g = 0 */
-    LW_WARD = 3      /* a_i = (n_i+n_k)/T, a_j = (n_j+n_k)/T, b = -n_k/T, g = 0 */
+    LW_WARD = 3,     /* a_i = (n_i+n_k)/T, a_j = (n_j+n_k)/T, b = -n_k/T, g = 0 */
+    LW_WEIGHTED = 4, /* weighted average: a_i = a_j = 1/2, b = g = 0 */
+    LW_CENTROID = 5  /* a_i = n_i/(n_i+n_j), a_j = n_j/(n_i+n_j),
+                        b = -n_i n_j/(n_i+n_j)^2, g = 0 (heights may decrease) */
 } lw_linkage;
 
 typedef enum {

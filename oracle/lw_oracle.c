@@ -50,7 +50,7 @@
 #include <omp.h>
 #endif
 
-enum { LWO_SINGLE = 0, LWO_COMPLETE = 1, LWO_AVERAGE = 2, LWO_WARD = 3 };
+enum { LWO_SINGLE = 0, LWO_COMPLETE = 1, LWO_AVERAGE = 2, LWO_WARD = 3, LWO_WEIGHTED = 4, LWO_CENTROID = 5 };
 enum { LWO_OK = 0, LWO_BAD_ARG = 1, LWO_BAD_INPUT = 2, LWO_NO_MEMORY = 3 };
 
 /* Flat index of cell (r, c), r < c, of the packed row-major upper triangle. */
@@ -98,6 +98,18 @@ void lwo_coefficients(int linkage, int64_t ni, int64_t nj, int64_t nk, float out
         b = -((float)nk / T);
         break;
     }
+    case LWO_WEIGHTED:
+        ai = 0.5f; aj = 0.5f;
+        break;
+    case LWO_CENTROID: {
+        /* beta = -n_i n_j / (n_i + n_j)^2: numerator and denominator are exact
+         * integers, each converted to float once, then one division */
+        float sum = (float)(ni + nj);
+        ai = (float)ni / sum;
+        aj = (float)nj / sum;
+        b = -((float)(ni * nj) / (float)((ni + nj) * (ni + nj)));
+        break;
+    }
     default:
         break;
     }
@@ -142,7 +154,7 @@ static int validate(float *D, int64_t cells)
 int lwo_naive(float *D, int64_t n, int linkage, int32_t *merges, float *heights,
               int64_t *scanned_per_iter)
 {
-    if (n < 1 || linkage < 0 || linkage > 3 || (n > 1 && (!D || !merges || !heights)))
+    if (n < 1 || linkage < 0 || linkage > 5 || (n > 1 && (!D || !merges || !heights)))
         return LWO_BAD_ARG;
     if (n == 1)
         return LWO_OK;
@@ -253,7 +265,7 @@ static uint64_t row_minimum(const float *D, int64_t n, const unsigned char *acti
 int lwo_cached(float *D, int64_t n, int linkage, int32_t *merges, float *heights,
                int64_t max_merges, int64_t *stats, double *times)
 {
-    if (n < 1 || linkage < 0 || linkage > 3 || (n > 1 && (!D || !merges || !heights)))
+    if (n < 1 || linkage < 0 || linkage > 5 || (n > 1 && (!D || !merges || !heights)))
         return LWO_BAD_ARG;
     if (stats)
         memset(stats, 0, 6 * sizeof(int64_t));

@@ -13,6 +13,8 @@ from .native import (  # noqa: F401
     LW_COMPLETE,
     LW_AVERAGE,
     LW_WARD,
+    LW_WEIGHTED,
+    LW_CENTROID,
     lw_create,
     lw_cluster,
     lw_cluster_async,

@@ -292,7 +292,7 @@ lw_status check_args(lw_ctx *ctx, const float *dist, int64_t n, int linkage, con
         set_err(ctx, "n=%lld out of range [1, %d]", (long long)n, LW_MAX_N);
         return LW_ERR_INVALID_ARG;
     }
-    if (linkage < LW_SINGLE || linkage > LW_WARD) {
+    if (linkage < LW_SINGLE || linkage > LW_CENTROID) {
         set_err(ctx, "unknown linkage %d", linkage);
         return LW_ERR_INVALID_ARG;
     }
@@ -632,7 +632,7 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
     long long big_n = 0;
     for (int q = 0; q < njobs; ++q) {
         const lw_job &J = jobs[q];
-        if (J.n < 1 || J.n > LW_MAX_N || J.linkage < LW_SINGLE || J.linkage > LW_WARD ||
+        if (J.n < 1 || J.n > LW_MAX_N || J.linkage < LW_SINGLE || J.linkage > LW_CENTROID ||
             (J.n > 1 && (!is_device_ptr(J.dist) || !is_device_ptr(J.merges_out) ||
                          !is_device_ptr(J.heights_out)))) {
             set_err(ctx, "job %d: bad n, linkage or a pointer that is not device memory", q);

@@ -250,16 +250,22 @@ __device__ __forceinline__ float lw_cell(int linkage, float dki, float dkj, floa
         ga = -0.5f;
     } else if (linkage == 1) {
         ga = 0.5f;
-    } else if (linkage == 2) {
+    } else if (linkage == 2 || linkage == 5) {
+        // group average; centroid adds beta = -n_i n_j / (n_i + n_j)^2 (exact
+        // integers, each converted to float once, one division)
         const float sum = (float)(ni + nj);
         ai = __fdiv_rn((float)ni, sum);
         aj = __fdiv_rn((float)nj, sum);
-    } else {
+        if (linkage == 5)
+            be = -__fdiv_rn(__ll2float_rn((long long)ni * nj),
+                            __ll2float_rn((long long)(ni + nj) * (ni + nj)));
+    } else if (linkage == 3) {
         const float T = (float)(ni + nj + nk);
         ai = __fdiv_rn((float)(ni + nk), T);
         aj = __fdiv_rn((float)(nj + nk), T);
         be = -__fdiv_rn((float)nk, T);
     }
+    // linkage 4, weighted average: 1/2, 1/2, 0, 0
     float s = __fmul_rn(ai, dki);
     s = __fadd_rn(s, __fmul_rn(aj, dkj));
     s = __fadd_rn(s, __fmul_rn(be, dij));

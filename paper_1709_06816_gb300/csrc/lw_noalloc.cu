@@ -66,7 +66,7 @@ bool is_device_memory(const void *p)
 extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int32_t *merges_out,
                                         float *heights_out, void *cuda_stream)
 {
-    if (n < 1 || n > kNoAllocMaxN || linkage < LW_SINGLE || linkage > LW_WARD)
+    if (n < 1 || n > kNoAllocMaxN || linkage < LW_SINGLE || linkage > LW_CENTROID)
         return LW_ERR_INVALID_ARG;
     if (n == 1)
         return LW_OK;

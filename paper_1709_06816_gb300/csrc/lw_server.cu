@@ -344,7 +344,7 @@ lw_status lw_server_create(int device, int64_t budget_bytes, int32_t lanes, lw_s
 lw_status lw_server_submit(lw_server *s, const float *dist, int64_t n, int linkage,
                            int32_t *merges_out, float *heights_out, uint64_t *ticket)
 {
-    if (!s || !ticket || n < 1 || n > LW_MAX_N || linkage < LW_SINGLE || linkage > LW_WARD ||
+    if (!s || !ticket || n < 1 || n > LW_MAX_N || linkage < LW_SINGLE || linkage > LW_CENTROID ||
         (n > 1 && (!dist || !merges_out || !heights_out)))
         return LW_ERR_INVALID_ARG;
     Request r;

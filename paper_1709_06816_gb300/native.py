@@ -18,8 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblw.so")
 
-LW_SINGLE, LW_COMPLETE, LW_AVERAGE, LW_WARD = 0, 1, 2, 3
-LINKAGES = {"single": 0, "complete": 1, "average": 2, "ward": 3}
+LW_SINGLE, LW_COMPLETE, LW_AVERAGE, LW_WARD, LW_WEIGHTED, LW_CENTROID = 0, 1, 2, 3, 4, 5
+LINKAGES = {"single": 0, "complete": 1, "average": 2, "ward": 3, "weighted": 4, "centroid": 5}
 LW_OPT_GRID, LW_OPT_TIMEOUT_MS = 1, 2
 STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW_ERR_OOM",
           4: "LW_ERR_CUDA", 5: "LW_ERR_TIMEOUT", 6: "LW_ERR_BUSY"}

@@ -18,5 +18,5 @@ from .generators import (  # noqa: F401
     job_points,
     job_matrix,
     serve_requests,
-    SINGLE, COMPLETE, AVERAGE, WARD, LINKAGE_NAMES,
+    SINGLE, COMPLETE, AVERAGE, WARD, WEIGHTED, CENTROID, LINKAGE_NAMES,
 )

@@ -31,8 +31,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Linkage codes shared with the C interfaces (Table 1 rows used here).
-SINGLE, COMPLETE, AVERAGE, WARD = 0, 1, 2, 3
-LINKAGE_NAMES = {SINGLE: "single", COMPLETE: "complete", AVERAGE: "average", WARD: "ward"}
+SINGLE, COMPLETE, AVERAGE, WARD, WEIGHTED, CENTROID = 0, 1, 2, 3, 4, 5
+LINKAGE_NAMES = {SINGLE: "single", COMPLETE: "complete", AVERAGE: "average", WARD: "ward",
+                 WEIGHTED: "weighted", CENTROID: "centroid"}
 
 
 def packed_size(n: int) -> int:

@@ -75,7 +75,8 @@ def member_linkage(M: np.ndarray, linkage: str, points: np.ndarray | None = None
     """Agglomerative clustering recomputing every cluster distance from members.
 
     linkage: 'single' (min over member pairs), 'complete' (max), 'average'
-    (mean), 'ward' (2 nA nB / (nA+nB) ||cA - cB||^2 from ``points``).
+    (mean), 'ward' (2 nA nB / (nA+nB) ||cA - cB||^2 from ``points``),
+    'centroid' (||cA - cB||^2 from ``points``).
     Minimum by (value, i, j) lexicographically over live slots i < j; slot i
     keeps the merged cluster.  Returns (merges (n-1, 2), heights float64,
     gaps float64) where gaps[t] is the distance between the smallest and the
@@ -101,6 +102,10 @@ def member_linkage(M: np.ndarray, linkage: str, points: np.ndarray | None = None
                     ca = points[A].mean(axis=0)
                     cb = points[B].mean(axis=0)
                     v = 2.0 * len(A) * len(B) / (len(A) + len(B)) * float(((ca - cb) ** 2).sum())
+                elif linkage == "centroid":
+                    ca = points[A].mean(axis=0)
+                    cb = points[B].mean(axis=0)
+                    v = float(((ca - cb) ** 2).sum())
                 else:
                     raise ValueError(linkage)
                 if best is None or v < best[0]:

@@ -49,12 +49,15 @@ def lw_cell(linkage, dki, dkj, dij, ni, nj, nk):
         ga = f32(-0.5)
     elif linkage == 1:
         ga = f32(0.5)
-    elif linkage == 2:
+    elif linkage in (2, 5):
         sm = f32(ni + nj)
         ai, aj = f32(ni) / sm, f32(nj) / sm
-    else:
+        if linkage == 5:
+            be = -(f32(ni * nj) / f32((ni + nj) * (ni + nj)))
+    elif linkage == 3:
         t = f32(ni + nj + nk)
         ai, aj, be = f32(ni + nk) / t, f32(nj + nk) / t, -(f32(nk) / t)
+    # 4, weighted average: 1/2, 1/2, 0, 0
     s = f32(ai * dki)
     s = f32(s + f32(aj * dkj))
     s = f32(s + f32(be * dij))

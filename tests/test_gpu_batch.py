@@ -34,7 +34,7 @@ def _mixed_jobs(count, seed, n_lo=2, n_hi=700):
     out = []
     for q in range(count):
         n = int(rng.integers(n_lo, n_hi + 1))
-        link = int(rng.integers(0, 4))
+        link = int(rng.integers(0, 6))
         D = synth.small_gmm(n, 1000 * seed + q, dim=6, k=5) if q % 3 else synth.tie_heavy(n, q, 6)
         out.append((D, n, link))
     return out

@@ -55,7 +55,7 @@ def _assert_same(got, want, what=""):
 SMALL_N = [2, 3, 4, 5, 17, 31, 32, 33, 63, 64, 65, 100, 257, 300]
 
 
-@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("link", range(6))
 @pytest.mark.parametrize("kind", ["gmm", "ties"])
 def test_small_single_cta(ctx, link, kind):
     for s, n in enumerate(SMALL_N):
@@ -63,7 +63,7 @@ def test_small_single_cta(ctx, link, kind):
         _assert_same(_gpu(ctx, D, n, link, grid=1), oracle.cached(D, n, link), f"n={n}")
 
 
-@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("link", range(6))
 @pytest.mark.parametrize("grid", [2, 3, 7, 32])
 def test_small_multi_cta(ctx, link, grid):
     """The grid-barrier path at sizes that span several row blocks and a ragged tail."""
@@ -80,7 +80,7 @@ def test_layouts(ctx, layout):
     ctx.set_layout(layout)
     try:
         for s, n in enumerate([3, 33, 100, 257, 1000, 2100]):
-            for link in range(4):
+            for link in range(6):
                 D = synth.small_gmm(n, 500 + s) if (s + link) % 2 else synth.tie_heavy(n, 500 + s, levels=4)
                 want = oracle.cached(D, n, link)
                 for grid in (1, 7, 40):

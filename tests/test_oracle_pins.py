@@ -18,7 +18,8 @@ import synth
 from tests import brute
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-LINK = {"single": 0, "complete": 1, "average": 2, "ward": 3}
+LINK = {"single": 0, "complete": 1, "average": 2, "ward": 3, "weighted": 4, "centroid": 5}
+SQUARED = ("ward", "centroid")  # the closed forms hold for squared Euclidean distances
 
 
 def _bits(a):
@@ -96,6 +97,70 @@ def test_ward_update_matches_centroid_form():
         assert abs(float(got) - float(lw)) <= 10 * 2.0 ** -24 * mag
 
 
+def test_weighted_average_is_midpoint():
+    """Weighted average (Table 1): the new distance is (D(k,i) + D(k,j)) / 2
+    whatever the sizes -- exact on the dyadic grid."""
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 1 << 22, 500) / 1024.0
+    b = rng.integers(0, 1 << 22, 500) / 1024.0
+    for x, y in zip(a, b):
+        ni, nj, nk = (int(v) for v in rng.integers(1, 50, 3))
+        assert oracle.update(4, x, y, min(x, y), ni, nj, nk) == np.float32((x + y) / 2)
+
+
+def test_centroid_update_matches_centroid_form():
+    """Centroid row of Table 1 on squared Euclidean distances gives the squared
+    distance between the merged cluster's centroid and the other one's
+    (checked in exact rationals on a line with integer centroids), and the
+    FP32 result stays within the rounding bound of that value."""
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        ni, nj, nk = (int(x) for x in rng.integers(1, 7, 3))
+        ci, cj, ck = (int(x) for x in rng.integers(-20, 20, 3))
+        dki, dkj, dij = Fraction((ck - ci) ** 2), Fraction((ck - cj) ** 2), Fraction((ci - cj) ** 2)
+        s = ni + nj
+        lw = Fraction(ni, s) * dki + Fraction(nj, s) * dkj - Fraction(ni * nj, s * s) * dij
+        cij = Fraction(ni * ci + nj * cj, s)
+        assert lw == (ck - cij) ** 2
+        got = oracle.update(5, float(dki), float(dkj), float(dij), ni, nj, nk)
+        mag = float(Fraction(ni, s) * dki + Fraction(nj, s) * dkj + Fraction(ni * nj, s * s) * dij)
+        assert abs(float(got) - float(lw)) <= 10 * 2.0 ** -24 * mag
+
+
+def test_centroid_clustering_matches_centroids():
+    """Centroid linkage of points (squared Euclidean input) merges the pair of
+    clusters with the nearest centroids, at their squared centroid distance,
+    until FP32 rounding can reorder a near-tie."""
+    for seed in range(3):
+        p = np.random.default_rng(20 + seed).normal(size=(32, 3)) * 4
+        iu = np.triu_indices(32, 1)
+        D = ((p[iu[0]] - p[iu[1]]) ** 2).sum(axis=1).astype(np.float32)
+        m, h, _, _ = oracle.cached(D, 32, 5)
+        bm, bh, gaps = brute.member_linkage(brute.unpack(D, 32), "centroid", points=p)
+        for t in range(31):
+            assert (m[t] == bm[t]).all(), (seed, t)
+            assert abs(float(h[t]) - bh[t]) <= 1e-4 * bh[t] + 1e-5, (seed, t)
+            if gaps[t] <= 1e-3 * bh[t]:
+                break
+
+
+def test_weighted_heights_lie_between_member_extremes():
+    """A weighted-average height is a weighted mean of member distances: at
+    every merge it lies between the closest and the furthest member pair of
+    the two clusters (brute force over members)."""
+    n = 40
+    D = synth.small_gmm(n, 9, dim=4, k=5)
+    M = brute.unpack(D, n).astype(np.float64)
+    m, h, _, _ = oracle.cached(D, n, 4)
+    members = {s: [s] for s in range(n)}
+    for t in range(n - 1):
+        i, j = int(m[t, 0]), int(m[t, 1])
+        block = M[np.ix_(members[i], members[j])]
+        tol = 8 * 2.0 ** -24 * block.max()
+        assert block.min() - tol <= float(h[t]) <= block.max() + tol, t
+        members[i] = members[i] + members.pop(j)
+
+
 # --------------------------------------------------------------------------
 # worked examples and the paper's counts
 # --------------------------------------------------------------------------
@@ -110,7 +175,7 @@ def test_line4_worked_dendrograms():
     for name, steps in want.items():
         iu = np.triu_indices(n, 1)
         d = np.array([abs(pts[a] - pts[b]) for a, b in zip(*iu)])
-        if name == "ward":
+        if name in SQUARED:
             d = d ** 2
         m, h, _ = oracle.naive(d.astype(np.float32), n, LINK[name])
         for t, (i, j, hv) in enumerate(steps):
@@ -123,7 +188,7 @@ def test_section5_counts():
     search of an iteration with m live clusters reads (m^2 - m)/2 cells."""
     (n, p, cells, per), = [[int(x) for x in r] for r in _read_golden("section5_partition.txt")]
     assert synth.packed_size(n) == cells and cells // p == per and cells % p == 0
-    for link in range(4):
+    for link in range(6):
         _, _, scanned = oracle.naive(synth.small_gmm(40, 3), 40, link)
         m = 40 - np.arange(39)
         assert (scanned == (m * m - m) // 2).all()
@@ -133,7 +198,7 @@ def test_tiny_cases():
     assert oracle.naive(np.zeros(0, np.float32), 1, 1)[0].shape == (0, 2)
     m, h, _ = oracle.naive(np.array([2.5], np.float32), 2, 0)
     assert m.tolist() == [[0, 1]] and h.tolist() == [2.5]
-    for link in range(4):
+    for link in range(6):
         # all distances equal: ties resolve to (0,1) then (0,2)
         m, h, _ = oracle.naive(np.ones(3, np.float32), 3, link)
         assert m.tolist() == [[0, 1], [0, 2]]
@@ -235,7 +300,7 @@ def test_ward_matches_centroid_brute_force(seed):
 # invariants and the cache
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("link", range(6))
 @pytest.mark.parametrize("kind", ["gmm", "ties"])
 def test_naive_equals_cached(link, kind):
     """The row-minimum cache changes nothing: bit-identical to the full search."""
@@ -247,7 +312,7 @@ def test_naive_equals_cached(link, kind):
         assert np.array_equal(_bits(a[1]), _bits(b[1]))
 
 
-@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("link", range(6))
 def test_structural_invariants(link):
     n = 200
     D = synth.small_gmm(n, 11, dim=6, k=6)
@@ -260,10 +325,11 @@ def test_structural_invariants(link):
         retired.add(j)
         sizes[i] += sizes.pop(j)
     assert list(sizes) == [0] and sizes[0] == n
-    # monotone heights: exact for single/complete; a few ulps for average/Ward
+    # monotone heights: exact for single/complete; a few ulps for average,
+    # Ward and weighted average; centroid linkage may invert (Table 1 note)
     if link in (0, 1):
         assert (np.diff(h) >= 0).all()
-    else:
+    elif link != 5:
         assert (h[1:] >= h[:-1] * (1 - 4 * 2.0 ** -24)).all()
     if link in (0, 1):
         C = brute.cophenetic(n, m, h.astype(np.float64))
@@ -307,9 +373,14 @@ MUTANTS = {
                           "ai = 0.5f; aj = 0.5f; b = 0.0f; g = 0.5f;"),
     "complete drops |a-b| term": ("ai = 0.5f; aj = 0.5f; b = 0.0f; g = 0.5f;",
                                   "ai = 0.5f; aj = 0.5f; b = 0.0f; g = 0.0f;"),
-    "average swaps sizes": ("ai = (float)ni / sum;", "ai = (float)nj / sum;"),
+    "average swaps sizes": ("case LWO_AVERAGE: {\n        float sum = (float)(ni + nj);\n        ai = (float)ni / sum;",
+                            "case LWO_AVERAGE: {\n        float sum = (float)(ni + nj);\n        ai = (float)nj / sum;"),
     "ward beta sign": ("b = -((float)nk / T);", "b = ((float)nk / T);"),
     "ward alpha_i uses n_j": ("ai = (float)(ni + nk) / T;", "ai = (float)(ni + nj) / T;"),
+    "centroid beta sign": ("b = -((float)(ni * nj) / (float)((ni + nj) * (ni + nj)));",
+                           "b = ((float)(ni * nj) / (float)((ni + nj) * (ni + nj)));"),
+    "weighted uses group-average weights": ("ai = 0.5f; aj = 0.5f;\n        break;\n    case LWO_CENTROID",
+                                            "ai = (float)ni / (float)(ni + nj); aj = (float)nj / (float)(ni + nj);\n        break;\n    case LWO_CENTROID"),
     "formula drops beta term": ("s = s + co[2] * dij;", "s = s + 0.0f * dij;"),
     "naive tie-break last": ("if (i < 0 || v < h) {", "if (i < 0 || v <= h) {"),
     "swapped operands": ("D[pi] = lw_formula(co, D[pi], D[pair_index(n, k, j)], h);",
@@ -333,7 +404,7 @@ def _pins_pass(lib) -> bool:
         rows = _read_golden("line4_dendrograms.txt")[1:]
         for r in rows:
             link = LINK[r[0]]
-            dd = (d ** 2 if r[0] == "ward" else d).astype(np.float32)
+            dd = (d ** 2 if r[0] in SQUARED else d).astype(np.float32)
             for res in (lib.naive(dd, 4, link), lib.cached(dd, 4, link)):
                 t = int(r[1])
                 if (res[0][t, 0], res[0][t, 1]) != (int(r[2]), int(r[3])):
@@ -348,7 +419,7 @@ def _pins_pass(lib) -> bool:
                     if not (np.array_equal(res[0], bm) and np.array_equal(res[1].astype(np.float64), bh)):
                         return False
         # naive vs cached on all linkages
-        for link in range(4):
+        for link in range(6):
             for D in (synth.small_gmm(90, 3), synth.tie_heavy(90, 4)):
                 a, b = lib.naive(D, 90, link), lib.cached(D, 90, link)
                 if not (np.array_equal(a[0], b[0]) and np.array_equal(_bits(a[1]), _bits(b[1]))):
@@ -365,13 +436,14 @@ def _pins_pass(lib) -> bool:
         p = np.random.default_rng(1).normal(size=(30, 3)) * 5
         iu = np.triu_indices(30, 1)
         D = ((p[iu[0]] - p[iu[1]]) ** 2).sum(axis=1).astype(np.float32)
-        m, h, _, _ = lib.cached(D, 30, 3)
-        bm, bh, gaps = brute.member_linkage(brute.unpack(D, 30), "ward", points=p)
-        for t in range(29):
-            if abs(float(h[t]) - bh[t]) > 1e-4 * bh[t] + 1e-5 or not (m[t] == bm[t]).all():
-                return False
-            if gaps[t] <= 1e-3 * bh[t]:
-                break
+        for name in ("ward", "centroid"):
+            m, h, _, _ = lib.cached(D, 30, LINK[name])
+            bm, bh, gaps = brute.member_linkage(brute.unpack(D, 30), name, points=p)
+            for t in range(29):
+                if abs(float(h[t]) - bh[t]) > 1e-4 * bh[t] + 1e-5 or not (m[t] == bm[t]).all():
+                    return False
+                if gaps[t] <= 1e-3 * bh[t]:
+                    break
     except oracle.OracleError:
         return False
     return True

@@ -18,7 +18,7 @@ def _bits(a):
 CASES = [(n, kind) for n in (2, 5, 33, 70) for kind in ("gmm", "ties")]
 
 
-@pytest.mark.parametrize("link", range(4))
+@pytest.mark.parametrize("link", range(6))
 @pytest.mark.parametrize("G,chain,pub,refill_at", [(1, 16, 16, 0), (3, 32, 4, 0), (3, 32, 4, 2)])
 def test_model_matches_oracle(link, G, chain, pub, refill_at):
     for s, (n, kind) in enumerate(CASES):
