@@ -556,6 +556,43 @@ def run_reference(args, world, rank, local):
     print(json.dumps(out), flush=True)
 
 
+def run_cta_sweep(args, local):
+    """Time of one clustering against the number of CTAs (the GPU analogue of
+    the paper's running time against processor count, Section 6), at the
+    paper's mean problem size n = 1968 (conformer-like chains), complete
+    linkage.  Prints one JSON line; every point is the best of five runs of
+    a synchronised lw_cluster call (host wall clock, launch included)."""
+    import torch
+    import synth
+    from paper_1709_06816_gb300 import Context
+    torch.cuda.set_device(local)
+    w = synth.workload(f"conformer{args.sweep_n}")
+    src = w.matrix(device=f"cuda:{local}")
+    work = src.clone()
+    ctx = Context(local)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks = (w.n + 31) // 32  # a grid holds at most one CTA per 32-row block
+    grids = sorted({min(g, sms, blocks) for g in (1, 2, 4, 8, 16, 32, 64, 128, sms)})
+    points = []
+    ref = None
+    for g in grids:
+        ctx.set_grid(g)
+        best = float("inf")
+        for _ in range(5):
+            work.copy_(src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m, h = ctx.cluster(work, w.n, LINKAGE)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        got = (m.cpu().numpy().tobytes(), h.cpu().numpy().tobytes())
+        ref = ref or got
+        points.append({"ctas": ctx.stats()["grid"], "ms": best * 1e3, "same_result": got == ref})
+    ctx.close()
+    print(json.dumps({"experiment": "clustering time vs CTAs", "n": w.n, "linkage": "complete",
+                      "data": "synthetic conformer-like chains", "points": points}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,6 +606,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--cta-sweep", action="store_true",
+                    help="instead of the benchmark: clustering time against the CTA count")
+    ap.add_argument("--sweep-n", type=int, default=1968)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload name (profiling uses smaller conformer<N> cases)")
     args = ap.parse_args(argv)
@@ -588,7 +628,11 @@ def main(argv=None):
                 __graft_entry__.build()
             barrier(world)
             __graft_entry__.build()
-            run_ours(args, world, rank, local)
+            if args.cta_sweep:
+                if rank == 0:
+                    run_cta_sweep(args, local)
+            else:
+                run_ours(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist
