@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liblw_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SINGLE, COMPLETE, AVERAGE, WARD = 0, 1, 2, 3
+SINGLE, COMPLETE, AVERAGE, WARD, WEIGHTED, CENTROID = 0, 1, 2, 3, 4, 5
 
 
 class OracleError(RuntimeError):
