@@ -142,7 +142,13 @@ lw_status lw_wait(lw_ctx *ctx);
  *       only), [11] refill service in the barrier window, [12] certification
  *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish;
  *   [14] rows rescanned at once by their owner (cache emptied),
- *   [15] live cells read by those rescans.
+ *   [15] live cells read by those rescans,
+ *   [16..23] with LW_OPT_PHASE_TIMES on, a finer split of [9], [12] and
+ *       [13] (same units): [16] reading the CTAs' records, [17] the walk
+ *       and refill installs, [18] the chain's sizes, stamps and member
+ *       cells, [19] the cross-CTA minima of the new cells, [20] the
+ *       certification, [21] bookkeeping and survivor caches, [22] pass 2,
+ *       [23] owner rescans.
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 
@@ -164,11 +170,16 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *   LW_OPT_CTA_THREADS  threads per CTA of lw_cluster's kernel: 128, 256 or
  *                     512 (0: 512).  Smaller CTAs suit small matrices run
  *                     side by side (several fit one SM);
- *   LW_OPT_LAYOUT     working matrix of lw_cluster: 0 or 2 the packed
- *                     triangle (dist itself), 1 a symmetric n x n copy
- *                     (4n^2 bytes held by the context, used when it fits in
- *                     half the free device memory, else the triangle).
- *                     Results are the same either way.
+ *   LW_OPT_LAYOUT     working matrix of a multi-CTA lw_cluster run: 0
+ *                     (default) or 1 the row-log layout -- a symmetric n x n
+ *                     copy whose rows are rewritten whole, an n x n log of
+ *                     each row's cells to later-merged slots and a stamp per
+ *                     slot (8n^2 bytes held by the context, used when they
+ *                     fit in half the free device memory, else the packed
+ *                     triangle), so that every merge moves contiguous words;
+ *                     2 the packed triangle (dist itself, no extra memory).
+ *                     One-CTA runs always use the packed triangle.  Results
+ *                     are the same either way.
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
 enum {

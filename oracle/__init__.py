@@ -13,6 +13,8 @@ Functions:
   cached(D, n, linkage)  -- the same loop with a per-row minimum cache.
   coefficients(...)      -- Table 1 (a_i, a_j, b, g) in FP32.
   update(...)            -- the Section 4 step-3 formula for one cell.
+  sample(D, n, linkage)  -- wall time of the cached loop on a bounded prefix
+                            (validation + the first K merges), for CPU baselines.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import ctypes
 import os
 import subprocess
 import threading
+import time
 
 import numpy as np
 
@@ -185,3 +188,30 @@ def threads() -> int:
 
 def set_threads(k: int) -> None:
     _load().lib.lwo_set_threads(int(k))
+
+
+def sample(D, n: int, linkage: int, target_s: float = 12.0) -> dict:
+    """Time the cached loop, as it stands, on validation + the first K merges
+    of ``D`` (left unchanged), K chosen from a 50-merge calibration so the
+    sample takes about ``target_s`` seconds.  The full-run time is estimated by
+    scaling the sample's loop time with the work of the whole run, sum over
+    merges of the live cluster count m_t = n - t.
+
+    Returns {"K", "t_init_s", "t_loop_s", "est_total_s", "wall_s", "cores"}.
+    """
+    D = np.asarray(D)
+    work = np.empty_like(D)
+    np.copyto(work, D)
+    _, _, _, (t_init, t_loop) = cached(work, n, linkage, max_merges=50, inplace=True)
+    per_merge = t_loop / 50.0
+    K = int(max(100, min(n - 1, (target_s - t_init) / max(per_merge, 1e-6))))
+    np.copyto(work, D)
+    w0 = time.perf_counter()
+    _, _, _, (t_init, t_loop) = cached(work, n, linkage, max_merges=K, inplace=True)
+    wall = time.perf_counter() - w0
+    del work
+    sum_all = n * (n + 1) / 2 - 1
+    sum_k = K * n - K * (K - 1) / 2
+    est_total = t_init + t_loop * sum_all / sum_k
+    return {"K": K, "t_init_s": t_init, "t_loop_s": t_loop, "est_total_s": est_total,
+            "wall_s": wall, "cores": threads()}

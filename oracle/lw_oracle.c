@@ -14,24 +14,29 @@
  *     distance from every other cluster k to the combined one with
  *         D(k, i+j) = a_i D(k,i) + a_j D(k,j) + b D(i,j) + g |D(k,i) - D(k,j)|,
  *     (4) outputs the current level of the tree.
- *   - Table 1: the coefficients (a_i, a_j, b, g) of single, complete, group
- *     average and Ward linkage.  Section 5.3 step 6 gives the complete-linkage
+ *   - Table 1: the coefficients (a_i, a_j, b, g) of its six rows: single,
+ *     complete, group average (UPGMA), weighted average (WPGMA), centroid
+ *     (UPGMC) and Ward linkage.  Section 5.3 step 6 gives the complete-linkage
  *     form .5 D(k,i) + .5 D(k,j) + .5 |D(k,i) - D(k,j)| the authors used.
  *   - Section 5.1 / Section 5.2: only the upper triangle of the symmetric matrix is
  *     stored; Section 5.3 step 6: the combined cluster keeps row/column i, row and
  *     column j are marked unused.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent (the kernel library takes the same ones):
  *   - storage and arithmetic are IEEE FP32, every operation rounded to nearest
  *     even, no fused multiply-add (build with -ffp-contract=off), the four
  *     terms added left to right in the order the formula prints them;
  *   - "For k = 1 to n" performs n - 1 merges (the n-th iteration has no pair);
  *   - ties in the minimum go to the lowest (i, j) in row-major order, i < j;
  *     the survivor keeps slot i and slot j retires;
- *   - group-average a_i = fl(n_i / (n_i + n_j)), a_j = fl(n_j / (n_i + n_j)),
- *     each one correctly rounded FP32 division of exact integer-valued
- *     floats; Ward a_i = fl((n_i+n_k)/T), a_j = fl((n_j+n_k)/T),
- *     b = -fl(n_k/T), T = n_i + n_j + n_k;
+ *   - group average (and centroid) a_i = fl(n_i / (n_i + n_j)),
+ *     a_j = fl(n_j / (n_i + n_j)), each one correctly rounded FP32 division
+ *     of exact integer-valued floats; Ward a_i = fl((n_i+n_k)/T),
+ *     a_j = fl((n_j+n_k)/T), b = -fl(n_k/T), T = n_i + n_j + n_k;
+ *   - centroid b = -fl(float(n_i n_j) / float((n_i + n_j)^2)): the two
+ *     integers computed exactly, each converted to FP32 once, one correctly
+ *     rounded division, then negated;
+ *   - weighted average (0.5, 0.5, 0, 0) whatever the sizes;
  *   - NaN, infinite and negative distances are rejected; -0 becomes +0.
  *
  * Two loops:

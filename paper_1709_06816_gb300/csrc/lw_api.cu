@@ -22,7 +22,7 @@ struct lw_ctx {
     int num_sms = 0;
     int grid_opt = 0;
     int cta_threads = lw::kThreads;  // CTA size of the merge kernel (128, 256, 512)
-    int layout_opt = 0;              // 0 automatic, 1 full symmetric matrix, 2 packed triangle
+    int layout_opt = 0;              // 0 automatic, 1 row-log layout, 2 packed triangle
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
     int phase_timing = 0;
@@ -200,14 +200,17 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
         return s;
     char *ws = static_cast<char *>(ctx->ws);
 
-    // On request the kernel works on a symmetric n x n copy: each merge then
-    // reads rows i and j as consecutive words instead of one scattered cell
-    // per row of the packed triangle, but must write the new column as well
-    // (one scattered word per row).  On GB300 the two cost about the same, so
-    // the packed triangle, which needs no extra memory, is the default.
+    // Row-log layout (multi-CTA grids): the kernel works on a symmetric n x n
+    // copy M whose rows it rewrites whole, plus an n x n log TL that holds
+    // each row's cells to later-merged slots, and a stamp per slot.  Every
+    // merge then reads and writes contiguous words instead of one scattered
+    // cell per row of the packed triangle; it costs 8 n^2 bytes of device
+    // memory, used (automatically or on request) when that fits in half the
+    // free memory; otherwise, and for one-CTA grids, the packed triangle.
     bool use_full = false;
-    const size_t full_bytes = (size_t)n * (size_t)n * sizeof(float);
-    if (ctx->layout_opt == 1) {
+    const size_t nn = (size_t)n * (size_t)lw::log_pitch(n) * sizeof(float);
+    const size_t full_bytes = 2 * nn + align256((size_t)n * sizeof(int));
+    if (ctx->layout_opt != 2 && G > 1) {
         size_t free_b = 0, total_b = 0;
         if (ctx->full_cap >= full_bytes) {
             use_full = true;
@@ -225,8 +228,11 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
 
     lw::MergeParams p;
     p.D = use_full ? static_cast<float *>(ctx->full) : ddist;
+    p.TL = use_full ? reinterpret_cast<float *>(static_cast<char *>(ctx->full) + nn) : nullptr;
+    p.stamp = use_full ? reinterpret_cast<int *>(static_cast<char *>(ctx->full) + 2 * nn) : nullptr;
     p.full = use_full ? 1 : 0;
     p.n = n;
+    p.pitch = use_full ? lw::log_pitch(n) : n;
     p.linkage = linkage;
     p.G = G;
     p.aligned16 = ((uintptr_t)p.D & 15u) == 0;
@@ -245,7 +251,7 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     // barrier, status and stats words are contiguous
     if ((e = cudaMemsetAsync(ws + L.zero, 0, L.total - L.zero, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
-    if (use_full && (e = lw::launch_expand(ddist, p.D, n, p.status, ctx->stream)) != cudaSuccess)
+    if (use_full && (e = lw::launch_expand(ddist, p.D, n, p.pitch, p.status, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "expand kernel launch");
     if ((e = lw::launch_merge(p, ctx->cta_threads, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaLaunchCooperativeKernel");

@@ -18,7 +18,7 @@ constexpr int kRefillAt = 0;             // ask for a refill when the cache hold
 constexpr int kSurvivorRefillAt = 1;     // the same for a survivor row right after its merge
 constexpr int kMaxReq = 256;             // refill requests served per round
 constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
-constexpr int kStats = 16;
+constexpr int kStats = 24;
 constexpr uint64_t kNoKey = ~0ull;
 
 // Column word of a published entry: the column, or one of two stop marks.
@@ -44,11 +44,20 @@ static_assert(sizeof(RecA) == 240, "record layout");
 
 struct MergeParams {
     float *D;                      // working matrix, rewritten in place: the packed
-                                   // upper triangle, or (full = 1) the symmetric n x n
-                                   // matrix row-major, both halves kept current
+                                   // upper triangle, or (full = 1) the row-log layout:
+                                   // D is an n x n row-major matrix M whose row x is
+                                   // current for every column y with stamp[y] <= stamp[x]
+    float *TL;                     // full = 1: n x n; TL[x * n + t] = the cell between x
+                                   // and the survivor of merge t, written at merge t
+    int *stamp;                    // full = 1: [n] merge that last rewrote each slot's
+                                   // row (-1: never); cell {x, y} lives in the row of the
+                                   // later-stamped slot, and in TL of the other one
     int full;
     long long n;
-    int linkage;                   // 0 single, 1 complete, 2 average, 3 Ward
+    long long pitch;               // full = 1: words per row of M and TL (n rounded up
+                                   // to a multiple of 4: rows start 16-byte aligned)
+    int linkage;                   // Table 1 row: 0 single, 1 complete, 2 group average,
+                                   // 3 Ward, 4 weighted average, 5 centroid
     int G;                         // CTAs in the persistent grid
     int aligned16;                 // D is 16-byte aligned (128-bit loads allowed)
     int32_t *merges;               // [2(n-1)] device
@@ -123,10 +132,14 @@ struct BatchParams {
     unsigned long long timeout_ns;
 };
 
-// Writes the symmetric n x n matrix `full` (row-major, diagonal untouched)
-// from the packed upper triangle `packed`, with -0 cells as +0; a NaN,
-// infinite or negative cell sets *status to kErrInput.
-cudaError_t launch_expand(const float *packed, float *full, long long n, int *status, cudaStream_t stream);
+// Writes the symmetric n x n matrix `full` (row-major, rows `pitch` words
+// apart, diagonal untouched) from the packed upper triangle `packed`, with
+// -0 cells as +0; a NaN, infinite or negative cell sets *status to kErrInput.
+cudaError_t launch_expand(const float *packed, float *full, long long n, long long pitch, int *status,
+                          cudaStream_t stream);
+
+// Row pitch (words) of the row-log layout's n x n matrices.
+inline long long log_pitch(long long n) { return (n + 3) & ~3LL; }
 
 // Bytes of dynamic shared memory the merge kernel needs for (n, G) with CTAs
 // of nt threads.

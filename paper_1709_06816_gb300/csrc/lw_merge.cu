@@ -91,13 +91,19 @@ __device__ __forceinline__ long long pair_idx(long long a, long long b, long lon
 // Row r of the working matrix: cell (r, c) at row_base + c (packed: c > r only).
 __device__ __forceinline__ long long row_base(const MergeParams &p, long long r)
 {
-    return p.full ? r * p.n : tri_off(r, p.n) - r - 1;
+    return p.full ? r * p.pitch : tri_off(r, p.n) - r - 1;
 }
 
-// Any copy of cell {x, y}, x != y.
-__device__ __forceinline__ long long cell_at(const MergeParams &p, long long x, long long y)
+
+// Cell {x, y} read directly (the cells between members of a round's chain).
+// Row-log layout: the cell is current in the row of M whose slot was stamped
+// later (both rows hold the input value while neither slot has merged).
+__device__ __forceinline__ float member_cell(const MergeParams &p, long long x, long long y)
 {
-    return p.full ? x * p.n + y : pair_idx(x, y, p.n);
+    if (!p.full)
+        return __ldcg(p.D + pair_idx(x, y, p.n));
+    const int sx = __ldcg(p.stamp + x), sy = __ldcg(p.stamp + y);
+    return sx >= sy ? __ldcg(p.D + x * p.pitch + y) : __ldcg(p.D + y * p.pitch + x);
 }
 
 __device__ __forceinline__ u64 make_key(float v, unsigned c)
@@ -303,7 +309,8 @@ struct Shared {
     float ph[S];
     int szi[S], szj[S];
     long long bi[S], bj[S];      // row bases of the members: cell (x, c) at b + c
-    u64 amin[S], hmin[S];        // this CTA's smallest new cell per pair (all k, k > i)
+    int si[S], sj[S];            // row-log layout: the members' stamps before the round
+    u64 wam[W][S], whm[W][S];    // per warp: smallest new cell per pair (all k, k > i)
     u64 gamin[S], ghmin[S];      // the same over all CTAs
     float Dm[2 * S][2 * S];      // D between members (2a = i_a, 2a + 1 = j_a)
     float X[S][S];               // cell (i_a, i_b) after merge a alone
@@ -573,6 +580,110 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
     block_topk(L, sh);
 }
 
+// block_row_topk in the row-log layout.  Row r's current cells are (a) r's
+// log at every merge q after r's stamp whose survivor c is still live and
+// has not merged again (vpos: this CTA's bitmap of such "latest" merges),
+// and (b) row r of M at every other live column.  Part (a) marks its columns
+// in the scratch bitmap `newer`, part (b) skips them; only c > r count.
+// Merges t0 .. t0 + L0 - 1 (the current round, L0 > 0 only after this CTA's
+// own pass 2) take their survivors from the round's chain in shared memory,
+// older ones from the merge list.  Result in sh.tko.
+template <int NT, int S>
+__device__ void block_row_topk_log(const MergeParams &p, long long r, const unsigned *bitmap,
+                                   const unsigned *vpos, unsigned *newer, Shared<NT, S> &sh, long long t0,
+                                   int L0, long long &live_cells)
+{
+    const long long n = p.n;
+    const long long nwords = (n + 31) / 32;
+    const int sr = __ldcg(p.stamp + r);
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
+    long long cnt = 0;
+    auto take = [&](float v, long long c) {
+        ++cnt;
+        if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
+            list_insert(L, make_key(v, (unsigned)c));
+    };
+    for (long long w = threadIdx.x; w < nwords; w += NT)
+        newer[w] = 0u;
+    __syncthreads();
+    // (a) the log: latest merges after r's stamp, eight positions in flight
+    const float *log = p.TL + r * p.pitch;
+    const long long t1 = t0 + L0;
+    {
+        constexpr int U = 8;
+        for (long long q0 = (long long)sr + 1 + threadIdx.x; q0 < t1; q0 += U * NT) {
+            float v[U];
+            int c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long q = q0 + (long long)u * NT;
+                c[u] = -1;
+                if (q < t1 && ((vpos[q >> 5] >> (q & 31)) & 1u)) {
+                    c[u] = q < t0 ? __ldcg(p.merges + 2 * q) : sh.pi[q - t0];
+                    v[u] = __ldcg(log + q);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= 0) {
+                    atomicOr(&newer[c[u] >> 5], 1u << (c[u] & 31));
+                    if (c[u] > r)
+                        take(v[u], c[u]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // (b) row r of M at live columns c > r not found in the log: 16-byte
+    // pieces (rows start 16-byte aligned), eight in flight per thread
+    const float *row = p.D + r * p.pitch;
+    auto cur = [&](long long c) { return ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 1u; };
+    long long c_a = (r + 4) & ~3LL;  // first multiple of 4 above r
+    if (c_a > n)
+        c_a = n;
+    const long long c_b = c_a + ((n - c_a) & ~3LL);
+    for (long long c = r + 1 + threadIdx.x; c < c_a; c += NT)
+        if (cur(c))
+            take(__ldcg(row + c), c);
+    for (long long c = c_b + threadIdx.x; c < n; c += NT)
+        if (cur(c))
+            take(__ldcg(row + c), c);
+    {
+        constexpr int U = 8;
+        const float4 *R4 = reinterpret_cast<const float4 *>(row);
+        const long long j1 = c_b >> 2;
+        for (long long j0 = (c_a >> 2) + threadIdx.x; j0 < j1; j0 += U * NT) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long j = j0 + (long long)u * NT;
+                v[u] = j < j1 ? __ldcg(R4 + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long j = j0 + (long long)u * NT;
+                if (j < j1) {
+                    const long long c = j << 2;
+                    const unsigned m4 = ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 15u;
+                    if (m4 & 1u)
+                        take(v[u].x, c);
+                    if (m4 & 2u)
+                        take(v[u].y, c + 1);
+                    if (m4 & 4u)
+                        take(v[u].z, c + 2);
+                    if (m4 & 8u)
+                        take(v[u].w, c + 3);
+                }
+            }
+        }
+    }
+    live_cells += cnt;
+    block_topk(L, sh);
+}
+
 // K smallest keys of row r over live columns, computed by one warp (the
 // rows of a one-CTA job are refreshed this way, several warps side by side).
 // Adds the live cells read to `live_cells`.  Result in out (all lanes).
@@ -655,6 +766,11 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     unsigned char *q0 = smem_raw;
     unsigned *bitmap = reinterpret_cast<unsigned *>(q0);
     q0 += (nwords * 4 + 15) & ~15LL;
+    // row-log layout: merges whose survivor is live and has not merged again
+    // (bit q), and a scratch bitmap of columns for the row scans
+    unsigned *vpos = reinterpret_cast<unsigned *>(q0);
+    unsigned *newer = vpos + nwords;
+    q0 += G > 1 ? (2 * nwords * 4 + 15) & ~15LL : 0;
     u64 *wkey = reinterpret_cast<u64 *>(q0);
     q0 += (size_t)G * PUB * 8;
     u64 *ck = reinterpret_cast<u64 *>(q0);
@@ -663,14 +779,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     q0 += (size_t)Rmax * 8;
     unsigned *wcol = reinterpret_cast<unsigned *>(q0);
     q0 += (size_t)G * PUB * 4;
-    float *kvs = reinterpret_cast<float *>(q0);  // [S][NT]: pass-1 values of each thread's first row
-    q0 += S > 16 ? (size_t)S * NT * 4 : 0;       // (up to 16 pairs they stay in registers)
+    // more than 16 pairs per round: pass-1 values of the rows of one chunk of
+    // NT owned rows, kvs[q * KVP + a] for chunk row q and pair a (up to 16
+    // pairs they stay in registers)
+    constexpr int KVP = S + 1;
+    float *kvs = reinterpret_cast<float *>(q0);
+    q0 += S > 16 ? (size_t)(Rmax < NT ? Rmax : NT) * KVP * 4 : 0;
     int *rsize = reinterpret_cast<int *>(q0);
     int *ccnt = rsize + Rmax;
     int *pend_t = ccnt + Rmax;
     int *pend_s = pend_t + Rmax;
     int *rlist = pend_s + Rmax;
-    unsigned char *mflag = reinterpret_cast<unsigned char *>(rlist + Rmax);
+    int *rstamp = rlist + Rmax;  // row-log layout: each owned row's stamp
+    unsigned char *mflag = reinterpret_cast<unsigned char *>(rstamp + Rmax);
+    unsigned char *okf = mflag + Rmax;  // [NT]: chunk row q got pass-1 values
 
     auto row_of = [&](int l) -> long long {
         return (long long)((long long)b + (long long)G * (l >> 5)) * kRowBlock + (l & 31);
@@ -701,6 +823,11 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
 
     // per-phase wall-clock totals of this CTA (thread 0), when timing is on
     u64 ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
+    // finer split: ph1 = xs0 (records) + xs1 (walk, installs) + xs2 (chain
+    // sizes, stamps, member cells); ph4 = xs3 (cross-CTA minima) + xs4
+    // (certification) + xs5 (bookkeeping, survivor caches); ph5 = xs6 (pass 2)
+    // + xs7 (owner rescans) + the publish
+    u64 xs0 = 0, xs1 = 0, xs2 = 0, xs3 = 0, xs4 = 0, xs5 = 0, xs6 = 0, xs7 = 0;
     u64 tmark = 0;
     auto lap = [&](u64 &acc) {
         if (p.timing && threadIdx.x == 0) {
@@ -783,14 +910,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     for (long long w = tid; w < nwords; w += NT) {
         const long long live_n = n - w * 32;
         bitmap[w] = live_n >= 32 ? 0xffffffffu : ((1u << live_n) - 1u);
+        if (G > 1)
+            vpos[w] = 0u;
     }
     for (int l = tid; l < R; l += NT) {
         rsize[l] = 1;
         pend_t[l] = -1;
+        rstamp[l] = -1;
         mflag[l] = 0;
     }
-    for (long long r = (long long)b * NT + tid; r < n; r += (long long)G * NT)
+    for (long long r = (long long)b * NT + tid; r < n; r += (long long)G * NT) {
         p.size_g[r] = 1;
+        if (p.full)
+            __stcg(p.stamp + r, -1);
+    }
     if (tid == 0) {
         sh.ninst = 0;
         sh.nexec = 0;
@@ -893,7 +1026,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         if (tid == 0)
             sh.nmyreq[par] = 0;
-        lap(ph1);
+        lap(xs0);
 
         if (warp == 0) {
             // ---- the walk: merge the G published lists in key order.  Lane
@@ -1011,7 +1144,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (lane < np2) {
                     const long long ia = sh.ppi[lane];
                     if (ia > row)
-                        xr = make_key(__ldcg(p.D + base + ia), (unsigned)ia);
+                        xr = make_key(__ldcg(p.full ? p.D + ia * p.pitch + row : p.D + base + ia), (unsigned)ia);
                 }
                 u64 xs[S];
 #pragma unroll
@@ -1053,6 +1186,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 st_installs += ninst;
         }
         __syncthreads();
+        lap(xs1);
         const int s = sh.np;
         {
             // every CTA read the same records and walked them the same way, so
@@ -1070,11 +1204,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
 
         // ---- the chain's sizes, member flags and the cells between members
-        if (tid < S) {
-            sh.amin[tid] = kNoKey;
-            sh.hmin[tid] = kNoKey;
-            sh.gamin[tid] = kNoKey;
-            sh.ghmin[tid] = kNoKey;
+        for (int e = tid; e < W * S; e += NT) {
+            sh.wam[e / S][e % S] = kNoKey;
+            sh.whm[e / S][e % S] = kNoKey;
         }
         if (tid < s) {
             sh.szi[tid] = __ldcg(p.size_g + sh.pi[tid]);
@@ -1082,6 +1214,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             const long long i = sh.pi[tid], j = sh.pj[tid];
             sh.bi[tid] = row_base(p, i);  // cell (i, c) at bi + c (packed: for c > i)
             sh.bj[tid] = row_base(p, j);
+            sh.si[tid] = p.full ? __ldcg(p.stamp + i) : 0;
+            sh.sj[tid] = p.full ? __ldcg(p.stamp + j) : 0;
         }
         if (tid < 2 * s) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
@@ -1104,7 +1238,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
                     const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                     const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                    dmv[q] = __ldcg(p.D + cell_at(p, mu, mv));
+                    dmv[q] = member_cell(p, mu, mv);
                 }
             }
         } else {
@@ -1113,14 +1247,14 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
                     const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                     const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                    const float d = __ldcg(p.D + cell_at(p, mu, mv));
+                    const float d = member_cell(p, mu, mv);
                     sh.Dm[u][v] = d;
                     sh.Dm[v][u] = d;
                 }
             }
         }
         __syncthreads();
-        lap(ph1);
+        lap(xs2);
 
         // ---- pass 1: new cells of every live k outside the chain (reads only),
         // the pairs in groups of 16; the values of each thread's first row are
@@ -1133,7 +1267,86 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         for (int a = 0; a < (KV_REG ? S : 1); ++a)
             kv[a] = 0.0f;
         bool kok = false;
-        if (s > 0) {
+        constexpr int PC = 8;  // pairs whose cells one thread loads at once
+        if constexpr (S > PG) {
+            // every owned row's new cells, a chunk of NT rows at a time (the
+            // last chunk first, so chunk 0 stays in kvs for pass 2); after each
+            // chunk, NT / S threads per pair take its smallest new cell over
+            // the chunk's rows (all k and k > i_a), then reduce across lanes
+            constexpr int TPP = NT / S;
+            const int ra = tid / TPP, rpart = tid % TPP;
+            u64 ma = kNoKey, mh = kNoKey;
+            if (s > 0) {
+                for (int l0 = ((R - 1) / NT) * NT; l0 >= 0; l0 -= NT) {
+                    const int l = l0 + tid;
+                    bool ok = false;
+                    long long k = 0;
+                    if (l < R) {
+                        k = row_of(l);
+                        ok = k < n && live(bitmap, k) && !mflag[l];
+                    }
+                    okf[tid] = ok;
+                    if (ok) {
+                        const int nk = rsize[l];
+                        const long long bk = row_base(p, k);
+                        const bool full = p.full;
+                        const int sk = full ? rstamp[l] : 0;
+                        float *kr = kvs + (size_t)tid * KVP;
+#pragma unroll 1
+                        for (int a0 = 0; a0 < s; a0 += PC) {
+                            float va[PC], vb[PC];
+#pragma unroll
+                            for (int u = 0; u < PC; ++u) {
+                                const int a = a0 + u;
+                                va[u] = 0.0f;
+                                vb[u] = 0.0f;
+                                if (a < s) {
+                                    if (full) {
+                                        va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                        vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                                    } else {
+                                        const long long i = sh.pi[a], j = sh.pj[a];
+                                        va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                        vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < PC; ++u) {
+                                const int a = a0 + u;
+                                if (a < s)
+                                    kr[a] = lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    if (ra < s) {
+                        const long long ia = sh.pi[ra];
+                        for (int q = rpart; q < NT && l0 + q < R; q += TPP) {
+                            if (!okf[q])
+                                continue;
+                            const long long kq = row_of(l0 + q);
+                            const u64 key = make_key(kvs[(size_t)q * KVP + ra], (unsigned)kq);
+                            ma = key < ma ? key : ma;
+                            if (kq > ia && key < mh)
+                                mh = key;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) {
+                const u64 x = __shfl_xor_sync(kFull, ma, o);
+                const u64 y = __shfl_xor_sync(kFull, mh, o);
+                ma = x < ma ? x : ma;
+                mh = y < mh ? y : mh;
+            }
+            if (rpart == 0) {
+                __stcg(p.recB + (size_t)b * 2 * kRound + ra, ma);
+                __stcg(p.recB + (size_t)b * 2 * kRound + kRound + ra, mh);
+            }
+        } else if (s > 0) {
             for (int l0 = 0; l0 < R; l0 += NT) {
                 const int l = l0 + tid;
                 bool ok = false;
@@ -1145,10 +1358,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     if (ok)
                         nk = rsize[l];
                 }
-                // cell (k, i): in the full matrix row i holds it (consecutive
-                // k of a warp read consecutive words); packed, row k for k < i
+                // cell (k, i): packed, row i for k > i (consecutive k of a warp
+                // read consecutive words) and row k for k < i; row-log layout,
+                // row i of M when i was stamped no earlier than k, else i's
+                // log at k's stamp (words of one contiguous range)
                 const long long bk = row_base(p, k);
                 const bool full = p.full;
+                const int sk = full && l < R ? rstamp[l] : 0;
 #pragma unroll
                 for (int a0 = 0; a0 < S; a0 += PG) {
                     if (a0 >= s)
@@ -1161,8 +1377,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         vb[u] = 0.0f;
                         if (ok && a < s) {
                             const long long i = sh.pi[a], j = sh.pj[a];
-                            va[u] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
-                            vb[u] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
+                            if (full) {
+                                va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                            } else {
+                                va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                            }
                         }
                     }
 #pragma unroll
@@ -1174,10 +1395,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         if (ok) {
                             const float v = lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
                             if (l0 == 0) {
-                                if (KV_REG)
-                                    kv[KV_REG ? a : 0] = v;
-                                else
-                                    kvs[a * NT + tid] = v;
+                                kv[KV_REG ? a : 0] = v;
                             }
                             ka = make_key(v, (unsigned)k);
                             if (k > sh.pi[a])
@@ -1194,11 +1412,12 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                             mh = kNoKey;
                         else
                             mh = warp_u64_min(kh);
+                        // each warp keeps its own minima (no shared-memory atomics)
                         if (lane == 0) {
-                            if (ma != kNoKey)
-                                atomicMin(&sh.amin[a], ma);
-                            if (mh != kNoKey)
-                                atomicMin(&sh.hmin[a], mh);
+                            if (ma < sh.wam[warp][a])
+                                sh.wam[warp][a] = ma;
+                            if (mh < sh.whm[warp][a])
+                                sh.whm[warp][a] = mh;
                         }
                     }
                 }
@@ -1217,10 +1436,19 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
             }
         }
-        __syncthreads();
-        if (tid < 2 * S)
-            __stcg(p.recB + (size_t)b * 2 * kRound + (tid < S ? tid : kRound + tid - S),
-                   tid < S ? sh.amin[tid] : sh.hmin[tid - S]);
+        if constexpr (S <= PG) {
+            __syncthreads();
+            if (tid < 2 * S) {
+                // this CTA's minima per pair: over its warps
+                const int a = tid % S;
+                u64 m = kNoKey;
+                for (int w = 0; w < W; ++w) {
+                    const u64 x = tid < S ? sh.wam[w][a] : sh.whm[w][a];
+                    m = x < m ? x : m;
+                }
+                __stcg(p.recB + (size_t)b * 2 * kRound + (tid < S ? tid : kRound + tid - S), m);
+            }
+        }
         lap(ph2);
         grid_arrive(p, epoch);
 
@@ -1253,7 +1481,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 const long long rr = sh.exec_row[s2];
                 if (rr < 0 || rr >= n - 1)
                     continue;  // the same for every thread of the CTA
-                block_row_topk(p, rr, bitmap, sh, st_fill_cells);
+                if (p.full)
+                    block_row_topk_log(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells);
+                else
+                    block_row_topk(p, rr, bitmap, sh, st_fill_cells);
                 if (tid < K / 2) {
                     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.parts + ((size_t)par * kMaxReq + s2) * K);
                     __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
@@ -1285,14 +1516,27 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 ma = x < ma ? x : ma;
                 mh = y < mh ? y : mh;
             }
-            if (lane < S && a < s) {
-                if (ma != kNoKey)
-                    atomicMin(&sh.gamin[a], ma);
-                if (mh != kNoKey)
-                    atomicMin(&sh.ghmin[a], mh);
+            // lanes below S of every warp hold the warp's minima per pair
+            if (lane < S) {
+                sh.wam[warp][lane] = ma;
+                sh.whm[warp][lane] = mh;
+            }
+            __syncthreads();
+            if (tid < 2 * S) {
+                const int a2 = tid % S;
+                u64 m = kNoKey;
+                for (int w = 0; w < W; ++w) {
+                    const u64 x = tid < S ? sh.wam[w][a2] : sh.whm[w][a2];
+                    m = x < m ? x : m;
+                }
+                if (tid < S)
+                    sh.gamin[a2] = m;
+                else
+                    sh.ghmin[a2] = m;
             }
         }
         __syncthreads();
+        lap(xs3);
         // certification: thread (p, a) takes the smallest cell that merge a
         // (a < p) rewrote as seen after merge p - 1; the S threads of p reduce
         // and compare with P_p
@@ -1338,6 +1582,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         __syncthreads();
         const int L = sh.nacc;
+        lap(xs4);
 
         // ---- bookkeeping of the L merges
         if (b == 0) {
@@ -1350,9 +1595,13 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             for (int e = tid; e < L * L; e += NT) {
                 const int a = e / L, c = e % L;
                 if (a < c) {
-                    __stcg(p.D + cell_at(p, sh.pi[a], sh.pi[c]), sh.C[a][c]);
-                    if (p.full)
-                        __stcg(p.D + cell_at(p, sh.pi[c], sh.pi[a]), sh.C[a][c]);
+                    if (p.full) {
+                        // merge c, the later one, rewrites row i_c; i_a's log at merge c
+                        __stcg(p.D + (long long)sh.pi[c] * p.pitch + sh.pi[a], sh.C[a][c]);
+                        __stcg(p.TL + (long long)sh.pi[a] * p.pitch + t + c, sh.C[a][c]);
+                    } else {
+                        __stcg(p.D + pair_idx(sh.pi[a], sh.pi[c], n), sh.C[a][c]);
+                    }
                 }
             }
             // each pair a < c stands for three updates of the step-by-step
@@ -1363,6 +1612,19 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         if (tid < L) {
             const int j = sh.pj[tid];
             atomicAnd(&bitmap[j >> 5], ~(1u << (j & 31)));  // Section 4 step 2: slot j retires
+            // row-log layout: merge t + tid rewrites row i (every CTA writes the
+            // same value, so each one sees the new stamps in its own rescans)
+            if (p.full) {
+                __stcg(p.stamp + sh.pi[tid], (int)(t + tid));
+                // the members' earlier merges are no longer the latest; this one is
+                const int si = sh.si[tid], sj = sh.sj[tid];
+                if (si >= 0)
+                    atomicAnd(&vpos[si >> 5], ~(1u << (si & 31)));
+                if (sj >= 0)
+                    atomicAnd(&vpos[sj >> 5], ~(1u << (sj & 31)));
+                const long long q = t + tid;
+                atomicOr(&vpos[q >> 5], 1u << (q & 31));
+            }
         }
         if (tid >= 2 * L && tid < 2 * s) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
@@ -1392,6 +1654,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 // the survivor's cache: its smallest new cell outside the chain
                 // and, below it, the new cells to chain members
                 const int l = slot_of(ia);
+                rstamp[l] = (int)(t + a);
                 const u64 m = sh.ghmin[a];
                 u64 M[K];
 #pragma unroll
@@ -1442,7 +1705,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         __syncthreads();
-        lap(ph4);
+        lap(xs5);
 
         // ---- pass 2: apply the L merges to every live k outside them (in a
         // round without merges it only renews refill requests that the
@@ -1463,68 +1726,114 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (!ok)
                     continue;
                 // rows outside the chain kept their pass-1 values; rows of
-                // pairs the round did not merge, and rows past a thread's
-                // first, compute them now
-                const bool have = l0 == 0 && kok;
+                // pairs the round did not merge, and rows past the first
+                // chunk, compute them now
                 const long long bk = row_base(p, k);
                 const bool full = p.full;
+                const int sk = full ? rstamp[l] : 0;
                 u64 Cc[K];
                 cache_load(Cc, l);
                 int c = ccnt[l];
                 u64 B = cB[l];
+                // merge a gave row k the new cell v = D(k, i_a + j_a): store it
+                // and keep the cache
+                auto apply = [&](int a, float v) {
+                    const long long ia = sh.pi[a], ja = sh.pj[a];
+                    if (full) {
+                        // row i_a is rewritten whole; row k keeps its stale copy
+                        // and the new value goes to k's log at this merge
+                        __stcg(p.D + sh.bi[a] + k, v);
+                        __stcg(p.TL + bk + t + a, v);
+                    } else {
+                        __stcg(p.D + (k > ia ? sh.bi[a] + k : bk + ia), v);
+                    }
+                    ++st_updates;
+                    if (k < ja) {
+                        // row k loses column j; if k < i its cell (k, i) changed as well
+                        bool drop = false;
 #pragma unroll
-                for (int a0 = 0; a0 < S; a0 += PG) {
-                    if (a0 >= L)
-                        break;
-                    float va[PG], vb[PG];
-#pragma unroll
-                    for (int u = 0; u < PG; ++u) {
-                        const int a = a0 + u;
-                        va[u] = 0.0f;
-                        vb[u] = 0.0f;
-                        if (!have && a < L) {
-                            const long long i = sh.pi[a], j = sh.pj[a];
-                            va[u] = __ldcg(p.D + (full || k > i ? sh.bi[a] + k : bk + i));
-                            vb[u] = __ldcg(p.D + (full || k > j ? sh.bj[a] + k : bk + j));
+                        for (int q = 0; q < K; ++q) {
+                            const long long col = (long long)(unsigned)Cc[q];
+                            if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia))) {
+                                Cc[q] = kNoKey;
+                                drop = true;
+                            }
+                        }
+                        if (drop) {
+                            close_holes(Cc);
+                            c = list_count(Cc);
+                        }
+                        if (k < ia) {
+                            const u64 x = make_key(v, (unsigned)ia);
+                            if (x <= B) {
+                                list_insert(Cc, x);
+                                if (c == K)
+                                    B = Cc[K - 1];
+                                else
+                                    ++c;
+                            }
                         }
                     }
+                };
+                if constexpr (S > PG) {
+                    if (l0 == 0 && okf[tid]) {
+                        const float *kr = kvs + (size_t)tid * KVP;
+#pragma unroll 1
+                        for (int a = 0; a < L; ++a)
+                            apply(a, kr[a]);
+                    } else {
+#pragma unroll 1
+                        for (int a0 = 0; a0 < L; a0 += PC) {
+                            float va[PC], vb[PC];
 #pragma unroll
-                    for (int u = 0; u < PG; ++u) {
-                        const int a = a0 + u;
-                        if (a >= L)
+                            for (int u = 0; u < PC; ++u) {
+                                const int a = a0 + u;
+                                va[u] = 0.0f;
+                                vb[u] = 0.0f;
+                                if (a < L) {
+                                    if (full) {
+                                        va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                        vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                                    } else {
+                                        const long long i = sh.pi[a], j = sh.pj[a];
+                                        va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                        vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < PC; ++u) {
+                                const int a = a0 + u;
+                                if (a < L)
+                                    apply(a, lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk));
+                            }
+                        }
+                    }
+                } else {
+                    const bool have = l0 == 0 && kok;
+#pragma unroll
+                    for (int a0 = 0; a0 < S; a0 += PG) {
+                        if (a0 >= L)
                             break;
-                        const long long ia = sh.pi[a], ja = sh.pj[a];
-                        const float v = have ? (KV_REG ? kv[KV_REG ? a : 0] : kvs[a * NT + tid])
-                                             : lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk);
-                        __stcg(p.D + (full || k > ia ? sh.bi[a] + k : bk + ia), v);
-                        if (full)
-                            __stcg(p.D + bk + ia, v);  // the copy in row k
-                        ++st_updates;
-                        if (k < ja) {
-                            // row k loses column j; if k < i its cell (k, i) changed as well
-                            bool drop = false;
+                        float va[PG], vb[PG];
 #pragma unroll
-                            for (int q = 0; q < K; ++q) {
-                                const long long col = (long long)(unsigned)Cc[q];
-                                if (Cc[q] != kNoKey && (col == ja || (k < ia && col == ia))) {
-                                    Cc[q] = kNoKey;
-                                    drop = true;
-                                }
+                        for (int u = 0; u < PG; ++u) {
+                            const int a = a0 + u;
+                            va[u] = 0.0f;
+                            vb[u] = 0.0f;
+                            if (!have && a < L) {
+                                const long long i = sh.pi[a], j = sh.pj[a];
+                                va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
                             }
-                            if (drop) {
-                                close_holes(Cc);
-                                c = list_count(Cc);
-                            }
-                            if (k < ia) {
-                                const u64 x = make_key(v, (unsigned)ia);
-                                if (x <= B) {
-                                    list_insert(Cc, x);
-                                    if (c == K)
-                                        B = Cc[K - 1];
-                                    else
-                                        ++c;
-                                }
-                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < PG; ++u) {
+                            const int a = a0 + u;
+                            if (a >= L)
+                                break;
+                            apply(a, have ? kv[KV_REG ? a : 0]
+                                          : lw_cell(p.linkage, va[u], vb[u], sh.ph[a], sh.szi[a], sh.szj[a], nk));
                         }
                     }
                 }
@@ -1548,6 +1857,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         __syncthreads();
+        lap(xs6);
         // ---- rows whose cache emptied (one-CTA job: also survivors and rows
         // running low, a warp each)
         if (G == 1) {
@@ -1570,7 +1880,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             const int nresc = sh.nresc;
             for (int q = 0; q < nresc; ++q) {
                 const int l = rlist[q];
-                block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
+                if (p.full)
+                    block_row_topk_log(p, row_of(l), bitmap, vpos, newer, sh, t, L, st_resc_cells);
+                else
+                    block_row_topk(p, row_of(l), bitmap, sh, st_resc_cells);
                 if (tid == 0) {
                     cache_store(l, sh.tko);
                     const int c = list_count(sh.tko);
@@ -1587,6 +1900,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (owner_of(m) == b)
                 mflag[slot_of(m)] = 0;
         }
+        lap(xs7);
         if (tid < L) {
             sh.ppi[tid] = sh.pi[tid];
             sh.ppj[tid] = sh.pj[tid];
@@ -1626,12 +1940,18 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 St[4] = (u64)st_fills;
             }
             if (p.timing) {
+                ph1 += xs0 + xs1 + xs2;
+                ph4 += xs3 + xs4 + xs5;
+                ph5 += xs6 + xs7;
                 atomicAdd(St + 8, ph0);
                 atomicAdd(St + 9, ph1);
                 atomicAdd(St + 10, ph2);
                 atomicAdd(St + 11, ph3);
                 atomicAdd(St + 12, ph4);
                 atomicAdd(St + 13, ph5);
+                const u64 xs[8] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7};
+                for (int q = 0; q < 8; ++q)
+                    atomicAdd(St + 16 + q, xs[q]);
             }
         }
     }
@@ -1668,8 +1988,11 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
         const BatchJob J = bp.jobs[jb];
         MergeParams p;
         p.D = J.D;
+        p.TL = nullptr;
+        p.stamp = nullptr;
         p.full = 0;
         p.n = J.n;
+        p.pitch = J.n;
         p.linkage = J.linkage;
         p.G = 1;
         p.aligned16 = ((uintptr_t)J.D & 15u) == 0;
@@ -1701,7 +2024,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
 // written both as it is and transposed through shared memory, so every
 // global access of a warp is 32 consecutive words.
 __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ P, float *__restrict__ F,
-                                                     long long n, int *status)
+                                                     long long n, long long pitch, int *status)
 {
     __shared__ float tile[32][33];
     const long long tr = blockIdx.y, tc = blockIdx.x;
@@ -1719,7 +2042,7 @@ __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ P
                 v = 0.0f;  // -0 reads as +0 from here on
             else if (u > 0x7f7fffffu)
                 bad = 1;   // NaN, infinite or negative
-            F[r * n + c] = v;
+            F[r * pitch + c] = v;
         }
         tile[yy][tx] = v;
     }
@@ -1727,7 +2050,7 @@ __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ P
     for (int yy = ty; yy < 32; yy += 8) {
         const long long c = tc * 32 + yy, r = tr * 32 + tx;
         if (c > r && c < n)
-            F[c * n + r] = tile[tx][yy];
+            F[c * pitch + r] = tile[tx][yy];
     }
     if (bad)
         atomicCAS(status, 0, kErrInput);
@@ -1735,12 +2058,13 @@ __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ P
 
 }  // namespace
 
-cudaError_t launch_expand(const float *packed, float *full, long long n, int *status, cudaStream_t stream)
+cudaError_t launch_expand(const float *packed, float *full, long long n, long long pitch, int *status,
+                          cudaStream_t stream)
 {
     const long long nb = (n + 31) / 32;
     if (nb > 65535)
         return cudaErrorInvalidValue;
-    expand_kernel<<<dim3((unsigned)nb, (unsigned)nb), dim3(32, 8), 0, stream>>>(packed, full, n, status);
+    expand_kernel<<<dim3((unsigned)nb, (unsigned)nb), dim3(32, 8), 0, stream>>>(packed, full, n, pitch, status);
     return cudaGetLastError();
 }
 
@@ -1750,12 +2074,16 @@ size_t merge_smem_bytes(long long n, int G, int nt)
     const long long Rmax = ((nb + G - 1) / G) * kRowBlock;
     const long long nwords = (n + 31) / 32;
     // bitmap; published entries (keys, column words); per
-    // slot: K keys, bound, size, count, refill round and position, chain
-    // flag; pass-1 values of each thread's first row (one float per pair)
+    // slot: K keys, bound, size, count, refill round and position, rescan
+    // list entry, stamp, chain flag; pass-1 values of one chunk of rows (one
+    // float per pair) and their flags
     const long long pub = G == 1 ? kPubOne : kPub;
     const long long S = round_of((int)pub);
-    return (size_t)(((nwords * 4 + 15) & ~15LL) + (long long)G * pub * 12 + (S > 16 ? S * nt * 4 : 0) +
-                    ((Rmax * (8 * K + 8 + 4 * 5 + 1) + 15) & ~15LL));
+    const long long chunk = Rmax < nt ? Rmax : nt;
+    const long long logbits = G > 1 ? (2 * nwords * 4 + 15) & ~15LL : 0;
+    return (size_t)(((nwords * 4 + 15) & ~15LL) + logbits + (long long)G * pub * 12 +
+                    (S > 16 ? chunk * (S + 1) * 4 : 0) +
+                    ((Rmax * (8 * K + 8 + 4 * 6 + 1) + nt + 15) & ~15LL));
 }
 
 namespace {

@@ -102,8 +102,11 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
 
     lw::MergeParams p;
     p.D = dist;
+    p.TL = nullptr;
+    p.stamp = nullptr;
     p.full = 0;
     p.n = n;
+    p.pitch = n;
     p.linkage = linkage;
     p.G = G;
     p.aligned16 = ((uintptr_t)dist & 15u) == 0;

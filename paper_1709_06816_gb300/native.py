@@ -177,8 +177,8 @@ def lw_wait(ctx: int) -> None:
 
 def lw_get_stats(ctx: int) -> dict:
     lib = load()
-    a = (ctypes.c_int64 * 16)()
-    s = lib.lw_get_stats(ctx, a, 16)
+    a = (ctypes.c_int64 * 24)()
+    s = lib.lw_get_stats(ctx, a, 24)
     if s != 0:
         raise LwError(s, "lw_get_stats")
     out = {"rounds": a[0], "idle_rounds": a[1], "updated": a[2], "grid": a[3],
@@ -188,6 +188,9 @@ def lw_get_stats(ctx: int) -> dict:
         G = max(1, a[3])
         names = ("barrier", "walk", "pass1", "refill", "certify", "pass2")
         out["phase_ms"] = {nm: a[8 + q] / G / 1e6 for q, nm in enumerate(names)}
+        sub = ("records", "walk_installs", "chain", "minima", "certify", "bookkeeping", "pass2",
+               "rescans")
+        out["subphase_ms"] = {nm: a[16 + q] / G / 1e6 for q, nm in enumerate(sub)}
     return out
 
 
@@ -350,7 +353,8 @@ class Context:
             raise LwError(s, f"lw_set_batch_classes({classes})")
 
     def set_layout(self, layout: int):
-        """0 automatic, 1 symmetric n x n working copy, 2 packed triangle."""
+        """0 automatic (row-log layout for multi-CTA runs when it fits), 1 row-log
+        layout, 2 packed triangle."""
         lw_set_option(self.handle, LW_OPT_LAYOUT, layout)
 
     def set_cta_threads(self, nt: int):

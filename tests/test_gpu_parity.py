@@ -75,8 +75,9 @@ def test_small_multi_cta(ctx, link, grid):
 
 @pytest.mark.parametrize("layout", [1, 2])
 def test_layouts(ctx, layout):
-    """The symmetric n x n working copy (1) and the packed triangle (2), on one
-    CTA and on several, against the oracle."""
+    """The row-log layout (1: symmetric rows rewritten whole, a log of each
+    row's cells to later-merged slots, stamps; multi-CTA runs only) and the
+    packed triangle (2), on one CTA and on several, against the oracle."""
     ctx.set_layout(layout)
     try:
         for s, n in enumerate([3, 33, 100, 257, 1000, 2100]):
