@@ -2,18 +2,22 @@
 """Benchmark of the Lance-Williams merge loop on GB300.
 
 A step is one whole clustering of the n = 65536 conformer-like matrix
-(complete linkage): the persistent kernel validates the 8.59 GB packed
-triangle, builds the row minima and performs all 65535 merges (Section 4's
-iteration).  The kernel rewrites the matrix in place, so every step first
-restores it from a pristine device copy (a device-to-device copy, counted
-inside the step).
+(complete linkage): the library validates the 8.59 GB packed triangle,
+builds its working layout and row minima and performs all 65535 merges
+(Section 4's iteration).  The kernels rewrite the matrix in place, so every
+step first restores it from a pristine device copy (a device-to-device copy,
+counted inside the step).
 
 Printed (rank 0, one JSON line): merges/s over K timed steps (CUDA events on
 the library's stream, W untimed warm-up steps), the dendrogram time, the
-HBM roofline fraction of the kernel (algorithmic bytes from the kernel's own
-counters), the CPU oracle's rate on a bounded sample, an end-to-end rate
-through the C ABI with host buffers, and the SM clocks sampled during the
-timed region.
+HBM roofline fraction of the merge kernel, a full-length parity check of the
+result against the oracle's stored digest, the CPU oracle's rate (a bounded
+sample, calibrated against a full oracle run), an end-to-end rate through
+the C ABI with host buffers, the SM clocks sampled during the timed region,
+and one block per other workload: the n = 65536 Ward run, the three
+n = 16384 linkages, the n = 512 run against the L2 roofline, the batched
+and the served workloads (each against the plain per-job path) and the
+clustering time against the CTA count at n = 1968.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -25,8 +29,8 @@ collective on the data path ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -42,17 +46,18 @@ LINKAGE = 1  # complete linkage, the paper's own choice (Section 5.3 step 6)
 METRIC = "merges/s at n=65536 (complete linkage, bit-exact)"
 UNIT = "merges/s"
 FALLBACK_HBM_GBS = 6800.0
+LINK_NAMES = {0: "single", 1: "complete", 2: "average", 3: "ward", 4: "weighted", 5: "centroid"}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one merge
-# kernel launch on the bench workload, from one ncu capture
-# (profiles/merge_kernel_conformer65536_dram.md).  It describes the kernel
-# code it was taken on (lw_merge.cu and lw_internal.h, comments aside) and is
-# reported only while that code is unchanged.
+# kernel launch on the bench workload, from one ncu capture of the bench's
+# launch.  It describes the kernel code it was taken on (lw_merge.cu and
+# lw_internal.h, comments aside) and is reported only while that code is
+# unchanged.
 MEASURED_TRAFFIC = {
     "workload": "conformer65536:1",
-    "kernel_sha256": "7bb81418a6bf71c046d2c280a2de8faefe851597d7d17e9cb8cb31936261f36e",
-    "bytes_per_launch": 370.61e9 + 35.09e9,
+    "kernel_sha256": "",
+    "bytes_per_launch": None,
 }
 
 
@@ -60,7 +65,6 @@ def kernel_source_sha256() -> str:
     """Hash of the merge kernel's code (the kernel and its constants), with
     // comments and blank space left out: an edit of the text around the code
     keeps a measurement valid, an edit of the code does not."""
-    import hashlib
     h = hashlib.sha256()
     for name in ("lw_merge.cu", "lw_internal.h"):
         with open(os.path.join(ROOT, "paper_1709_06816_gb300", "csrc", name), encoding="utf-8") as f:
@@ -76,7 +80,8 @@ def measured_traffic(workload: str, linkage: int):
         sha = kernel_source_sha256()
     except OSError:
         return None
-    if sha != MEASURED_TRAFFIC["kernel_sha256"] or f"{workload}:{linkage}" != MEASURED_TRAFFIC["workload"]:
+    if (sha != MEASURED_TRAFFIC["kernel_sha256"] or f"{workload}:{linkage}" != MEASURED_TRAFFIC["workload"]
+            or not MEASURED_TRAFFIC["bytes_per_launch"]):
         return None
     return MEASURED_TRAFFIC["bytes_per_launch"]
 
@@ -91,12 +96,13 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def work_counts(workload: str, linkage: int):
-    """The oracle's exact counters for this workload (bench_work_counts.json,
-    written by ``python -m oracle.work_counts``), or None."""
+def work_counts(key: str):
+    """The oracle's record for a workload ("name:linkage"): exact counters,
+    result digests and the CPU-sample calibration, written by
+    ``python -m oracle.work_counts``; None if absent."""
     try:
         with open(os.path.join(ROOT, "bench_work_counts.json")) as f:
-            return json.load(f).get(f"{workload}:{linkage}")
+            return json.load(f).get(key)
     except FileNotFoundError:
         return None
 
@@ -107,9 +113,10 @@ def algorithmic_bytes(n: int, linkage: int, counts) -> tuple:
     per merge t with m_t = n - t live clusters: read the m_t row keys (8 B),
     read D(k,i), D(k,j) and write D(k,i+j) for the m_t - 2 other clusters
     (12 B), Ward also reads m_t sizes (4 B), re-read every live cell of each
-    row whose cached minimum pointed at i or j and got worse (4 B; the count
-    is the oracle's, one cached key per row), and write the step (12 B).
-    Returns (bytes, note)."""
+    row whose cached minimum pointed at i or j and got worse, and the live
+    cells of the merged row i, whose minimum is recomputed (4 B each; the
+    counts are the oracle's, one cached key per row), and write the step
+    (12 B).  Returns (bytes, note)."""
     cells = n * (n - 1) // 2
     sum_m = n * (n + 1) // 2 - 1
     updated = (n - 1) * (n - 2) // 2  # sum over merges of m_t - 2
@@ -118,7 +125,27 @@ def algorithmic_bytes(n: int, linkage: int, counts) -> tuple:
         b += 4 * sum_m
     if counts is None:
         return b, "rescan term missing (no oracle counts for this workload)"
-    return b + 4 * int(counts["rescan_cells"]), "rescan term from the oracle's full run"
+    return (b + 4 * int(counts["rescan_cells"]) + 4 * int(counts.get("rowi_cells", 0)),
+            "rescan and row-i terms from the oracle's full run")
+
+
+def sha256_of(a) -> str:
+    """SHA-256 of an array's bytes in C order (the layout oracle.work_counts hashes)."""
+    import numpy as np
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def parity_block(merges, heights, key: str):
+    """Compare a whole GPU result with the oracle's stored digests of the
+    same workload (all n - 1 merges and heights, bit for bit)."""
+    rec = work_counts(key)
+    if rec is None or "merges_sha256" not in rec:
+        return {"oracle_sha_match": None, "note": f"no oracle digest for {key}"}
+    mm = sha256_of(merges) == rec["merges_sha256"]
+    hh = sha256_of(heights) == rec["heights_sha256"]
+    return {"oracle_sha_match": bool(mm and hh), "merges_match": bool(mm), "heights_match": bool(hh),
+            "reference": f"oracle full run ({rec.get('oracle_threads')} host threads, "
+                         f"{rec.get('oracle_seconds')} s), bench_work_counts.json[{key}]"}
 
 
 class ClockSampler:
@@ -200,37 +227,111 @@ def barrier(world: int):
         dist.barrier()
 
 
+def bench_config(n: int, world: int) -> dict:
+    """The workload description shared by both arms (same keys and values)."""
+    return {"workload": WORKLOAD, "n": n, "linkage": LINK_NAMES[LINKAGE],
+            "matrix_bytes": 4 * (n * (n - 1) // 2),
+            "l2": f"inputs larger than L2 ({4 * (n * (n - 1) // 2) / 1e9:.2f} GB packed triangle)",
+            "step": f"one clustering of the n={n} matrix: validate, row minima, {n - 1} merges",
+            "parallelism": f"replicas{world}"}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(D_host, n: int, linkage: int, target_s: float = 12.0):
-    """Run the oracle (as it stands) on init + the first K merges of the same
-    matrix, K chosen from a short calibration so the sample takes about
-    target_s seconds.  Returns (merges/s estimate for the whole run, info)."""
-    import numpy as np
+def oracle_rate(D_host, n: int, linkage: int, key: str, target_s: float):
+    """The oracle, as it stands, on a bounded prefix of the same matrix
+    (oracle.sample), its full-run time estimated by the work sum(m_t) and
+    then calibrated by the ratio that a full oracle run on this kind of host
+    showed between its true time and the same estimate.  Returns (merges/s,
+    info)."""
     import oracle
+    smp = oracle.sample(D_host, n, linkage, target_s=target_s)
+    rec = work_counts(key) or {}
+    cal = (rec.get("sample") or {}).get("full_over_est")
+    est = smp["est_total_s"]
+    full = est * cal if cal else est
+    info = dict(smp)
+    info.update({"calibration": cal, "calibrated_total_s": full,
+                 "uncalibrated_rate": (n - 1) / est})
+    return (n - 1) / full, info
 
-    work = np.empty_like(D_host)
-    np.copyto(work, D_host)
-    _, _, st, (t_init, t_loop) = oracle.cached(work, n, linkage, max_merges=50, inplace=True)
-    per_merge = t_loop / 50.0
-    K = int(max(100, min(n - 1, (target_s - t_init) / max(per_merge, 1e-6))))
-    np.copyto(work, D_host)
-    _, _, st, (t_init, t_loop) = oracle.cached(work, n, linkage, max_merges=K, inplace=True)
-    del work
-    # merge t costs about m_t = n - t; scale the sample's loop time by total work
-    sum_all = n * (n + 1) / 2 - 1
-    sum_k = sum(n - t for t in range(K))
-    est_total = t_init + t_loop * sum_all / sum_k
-    rate = (n - 1) / est_total
-    info = {"K": K, "t_init_s": t_init, "t_loop_s": t_loop, "est_total_s": est_total,
-            "cores": oracle.threads()}
-    return rate, info
+
+def cpu_sample_text(info, n):
+    cal = info["calibration"]
+    return (f"validation + first {info['K']} of {n - 1} merges of the same n={n} matrix on "
+            f"{info['cores']} host threads ({info['wall_s']:.1f} s); full-run time estimated by "
+            f"the work sum(m_t) ({info['est_total_s']:.1f} s)"
+            + (f" x {cal:.3f}, the ratio of a full oracle run's time to the same estimate "
+               f"({info['calibrated_total_s']:.1f} s)" if cal else " (no full-run calibration)"))
 
 
 # ---------------------------------------------------------------------------
-# arms
+# helpers of the GPU arm
+# ---------------------------------------------------------------------------
+
+def time_steps(ctx, stream, src, work, n, link, m_out, h_out, warmup, steps):
+    """W + K clusterings (restore + one launch each); returns the K kernel
+    times (ms, CUDA events around the launch) and the total (ms)."""
+    import torch
+
+    def step(ev=None):
+        with torch.cuda.stream(stream):
+            work.copy_(src)
+            if ev is not None:
+                ev[0].record(stream)
+            ctx.cluster_async(work, n, link, m_out, h_out)
+            if ev is not None:
+                ev[1].record(stream)
+        ctx.wait()
+
+    for _ in range(warmup):
+        step()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(steps):
+        step(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in kev], e0.elapsed_time(e1)
+
+
+def l2_probe(device: int):
+    """Measured L2 copy bandwidth: a device copy between two buffers that
+    together stay well inside L2, repeated back to back (read + write bytes
+    over CUDA-event time); the best of a few sizes."""
+    import torch
+    best = 0.0
+    l2 = torch.cuda.get_device_properties(device).L2_cache_size
+    for mb in (4, 8, 16):
+        nbytes = mb << 20
+        if 2 * nbytes > l2 // 2:
+            continue
+        a = torch.ones(nbytes // 4, device=f"cuda:{device}")
+        b = torch.empty_like(a)
+        for _ in range(5):
+            b.copy_(a)
+        reps = 200
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        gbs = 2 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        best = max(best, gbs)
+        del a, b
+    return best
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
 # ---------------------------------------------------------------------------
 
 def run_ours(args, world, rank, local):
@@ -251,14 +352,15 @@ def run_ours(args, world, rank, local):
     ctx = Context(local, stream=stream)
     torch.cuda.synchronize()
 
-    def step(ev_pair=None):
+    # warm-up (untimed), then the timed steps with the clocks sampled
+    def step(ev=None):
         with torch.cuda.stream(stream):
             work.copy_(src)
-            if ev_pair is not None:
-                ev_pair[0].record(stream)
+            if ev is not None:
+                ev[0].record(stream)
             ctx.cluster_async(work, n, LINKAGE, m_out, h_out)
-            if ev_pair is not None:
-                ev_pair[1].record(stream)
+            if ev is not None:
+                ev[1].record(stream)
         ctx.wait()
 
     for _ in range(args.warmup):
@@ -266,7 +368,6 @@ def run_ours(args, world, rank, local):
     ref_m = m_out.clone()
     ref_h = h_out.clone()
     stats = ctx.stats()
-
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -286,6 +387,9 @@ def run_ours(args, world, rank, local):
     kernel_ms = [a.elapsed_time(b) for a, b in kev]
     deterministic = bool(torch.equal(ref_m, m_out) and torch.equal(ref_h, h_out))
     total_ms_max = max_over_ranks(total_ms, world)
+    key = f"{args.workload}:{LINKAGE}"
+    parity = parity_block(m_out.cpu().numpy(), h_out.cpu().numpy(), key)
+    parity["deterministic_across_steps"] = deterministic
 
     # end-to-end through the C ABI with host buffers (pinned input, host outputs)
     e2e = None
@@ -295,42 +399,58 @@ def run_ours(args, world, rank, local):
         hm = np.empty((n - 1, 2), dtype=np.int32)
         hh = np.empty(n - 1, dtype=np.float32)
         ctx2 = Context(local)
-        ctx2.cluster(host, n, LINKAGE, hm, hh)  # warm: allocates the device copy
+        ctx2.cluster(host, n, LINKAGE, hm, hh)  # warm: allocates the device buffers
         reps = max(1, min(3, args.steps))
         t0 = time.perf_counter()
         for _ in range(reps):
             ctx2.cluster(host, n, LINKAGE, hm, hh)
         e2e_s = (time.perf_counter() - t0) / reps
-        e2e_ok = bool(np.array_equal(hm, ref_m.cpu().numpy()))
+        e2e_ok = bool(np.array_equal(hm, ref_m.cpu().numpy())
+                      and np.array_equal(hh.view(np.uint32), ref_h.cpu().numpy().view(np.uint32)))
         ctx2.close()
         del host
         e2e_s = max_over_ranks(e2e_s, world)
         e2e = {"value": world * (n - 1) / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 4 * (n * (n - 1) // 2),
-               "d2h_bytes_per_step": 12 * (n - 1) + 16 + 32,
-               "seconds_per_step": e2e_s, "matches_device_run": e2e_ok}
+               "d2h_bytes_per_step": 12 * (n - 1) + 16 + 8 * 24,
+               "seconds_per_step": e2e_s, "matches_device_run": e2e_ok,
+               "note": "lw_cluster with a pinned host matrix and host outputs: the upload, the "
+                       "clustering and the result copies inside the timed call"}
+
+    peak, peak_kind = peaks()
+    extra = {}
+    if world == 1 and not args.no_configs:
+        # the same matrix, Ward linkage (the other n = 65536 configuration)
+        km, _ = time_steps(ctx, stream, src, work, n, 3, m_out, h_out, 1, 3)
+        alg3, note3 = algorithmic_bytes(n, 3, work_counts(f"{args.workload}:3"))
+        k3 = sum(km) / len(km)
+        extra["conformer65536_ward"] = {
+            "n": n, "linkage": "ward", "dendrogram_ms": k3, "merges_per_s": (n - 1) / (k3 * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": alg3 / (k3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg3 / (k3 * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg3,
+                         "algorithmic_note": note3},
+            "parity": parity_block(m_out.cpu().numpy(), h_out.cpu().numpy(), f"{args.workload}:3")}
 
     # CPU oracle on a bounded sample of the same matrix (rank 0, N = 1 only)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         D_host = src.cpu().numpy()
-        del src
-        torch.cuda.empty_cache()
-        rate, info = oracle_sample(D_host, n, LINKAGE, target_s=args.cpu_seconds)
+        rate, info = oracle_rate(D_host, n, LINKAGE, key, args.cpu_seconds)
+        del D_host
         cpu = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-               "sample": (f"init + first {info['K']} of {n - 1} merges of the same n={n} matrix on "
-                          f"{info['cores']} host threads ({info['t_init_s']:.1f} s init, "
-                          f"{info['t_loop_s']:.1f} s merges); full-run time extrapolated by "
-                          f"work sum(m_t): {info['est_total_s']:.1f} s")}
+               "sample": cpu_sample_text(info, n), "uncalibrated_value": info["uncalibrated_rate"]}
 
     ctx.close()
-    del work
+    del work, src
     torch.cuda.empty_cache()
-    batched = None if args.no_batched else run_batched(args, local)
+    if world == 1 and not args.no_configs:
+        extra.update(run_other_configs(args, local, peak))
+    batched = None if args.no_batched else run_batched(args, local, peak)
     torch.cuda.empty_cache()
     serving = None if args.no_serving else run_serving(args, local)
-    peak, peak_kind = peaks()
-    alg, alg_note = algorithmic_bytes(n, LINKAGE, work_counts(args.workload, LINKAGE))
+    torch.cuda.empty_cache()
+    sweep = None if (args.no_sweep or world > 1) else run_cta_sweep(args, local)
+    alg, alg_note = algorithmic_bytes(n, LINKAGE, work_counts(key))
     k_avg_ms = sum(kernel_ms) / len(kernel_ms)
     achieved = alg / (k_avg_ms * 1e-3) / 1e9
     clocks = clk.summary()
@@ -347,41 +467,105 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "linkage": "complete",
-                   "matrix_bytes": 4 * (n * (n - 1) // 2),
-                   "l2": f"inputs larger than L2 ({4 * (n * (n - 1) // 2) / 1e9:.2f} GB packed triangle)",
-                   "step": "restore matrix (device copy) + one lw_cluster launch: validate, "
-                           f"row minima, {n - 1} merges",
-                   "grid_ctas": stats.get("grid"), "parallelism": f"replicas{world}"},
+        "config": bench_config(n, world),
         "dendrogram_ms": k_avg_ms,
         "kernel_ms": kernel_ms,
-        "deterministic_across_steps": deterministic,
+        "parity": parity,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(args.workload, LINKAGE),
                      "algorithmic_bytes_per_launch": alg, "algorithmic_note": alg_note,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "merge_kernel (one persistent cooperative launch per clustering)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * 2,
+        "gpu_launches_note": "per step: the layout kernel (symmetric copy of the triangle) and the "
+                             "persistent merge kernel",
         "clocks": clocks,
         "counters": stats,
+        "configs": extra,
         "batched": batched,
         "serving": serving,
+        "cta_sweep": sweep,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def run_batched(args, local, plain_sample: int = 256):
-    """The batched workload: 4096 independent jobs (n log-uniform in [64, 2048],
-    linkage uniform over the four, R^16 Gaussian mixtures) through one batch
-    plan (one persistent launch, work queue, CUDA graph), against the same jobs
-    through one lw_cluster call each on one stream (timed on a sample)."""
+def run_other_configs(args, local, peak):
+    """The other single-matrix configurations, each checked in full against
+    the oracle: n = 16384 (three linkages, distances on a 1/1024 grid: ties)
+    against the HBM roofline, and n = 512 (complete) against the L2
+    roofline (the matrix fits L2)."""
     import numpy as np
     import torch
 
+    import oracle
     import synth
-    from paper_1709_06816_gb300 import Context, native
+    from paper_1709_06816_gb300 import Context
+
+    out = {}
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream=stream)
+    try:
+        w = synth.workload("gmm16384q")
+        n = w.n
+        src = w.matrix(device=dev)
+        work = torch.empty_like(src)
+        m_out = torch.empty((n - 1, 2), dtype=torch.int32, device=dev)
+        h_out = torch.empty(n - 1, dtype=torch.float32, device=dev)
+        for link in (0, 1, 2):
+            km, _ = time_steps(ctx, stream, src, work, n, link, m_out, h_out, 2, 5)
+            k = sum(km) / len(km)
+            alg, note = algorithmic_bytes(n, link, work_counts(f"gmm16384q:{link}"))
+            out[f"gmm16384q_{LINK_NAMES[link]}"] = {
+                "n": n, "linkage": LINK_NAMES[link], "dendrogram_ms": k, "merges_per_s": (n - 1) / (k * 1e-3),
+                "roofline": {"bound": "hbm", "achieved": alg / (k * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": alg / (k * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+                             "algorithmic_note": note},
+                "parity": parity_block(m_out.cpu().numpy(), h_out.cpu().numpy(), f"gmm16384q:{link}")}
+        del src, work
+        torch.cuda.empty_cache()
+
+        w = synth.workload("gmm512")
+        n = w.n
+        D = w.matrix()
+        src = torch.from_numpy(D).to(dev)
+        work = torch.empty_like(src)
+        m_out = torch.empty((n - 1, 2), dtype=torch.int32, device=dev)
+        h_out = torch.empty(n - 1, dtype=torch.float32, device=dev)
+        km, _ = time_steps(ctx, stream, src, work, n, 1, m_out, h_out, 5, 50)
+        k = sum(km) / len(km)
+        wm, wh, st, _ = oracle.cached(D, n, 1)
+        same = bool(np.array_equal(m_out.cpu().numpy(), wm)
+                    and np.array_equal(h_out.cpu().numpy().view(np.uint32), wh.view(np.uint32)))
+        alg, _ = algorithmic_bytes(n, 1, st)
+        l2 = l2_probe(local)
+        out["gmm512_complete"] = {
+            "n": n, "linkage": "complete", "dendrogram_ms": k, "merges_per_s": (n - 1) / (k * 1e-3),
+            "roofline": {"bound": "l2", "achieved": alg / (k * 1e-3) / 1e9, "peak": l2, "unit": "GB/s",
+                         "frac": alg / (k * 1e-3) / 1e9 / l2, "algorithmic_bytes_per_launch": alg,
+                         "peak_source": "measured here: L2-resident device copy (read + write bytes)",
+                         "note": "one CTA (n <= 4096): a single SM works through 511 dependent merges"},
+            "parity": {"oracle_match": same, "reference": "oracle run here on the same matrix"}}
+    finally:
+        ctx.close()
+    return out
+
+
+def run_batched(args, local, peak, plain_sample: int = 256):
+    """The batched workload: 4096 independent jobs (n log-uniform in [64, 2048],
+    linkage uniform over the four, R^16 Gaussian mixtures) through one batch
+    plan (one persistent launch per size class, work queue, CUDA graph),
+    against the same jobs through one lw_cluster call each on one stream
+    (timed on a sample).  A sample of the jobs is checked against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_1709_06816_gb300 import Context, autotune, native
 
     dev = f"cuda:{local}"
     specs = synth.batch_jobs()
@@ -396,7 +580,6 @@ def run_batched(args, local, plain_sample: int = 256):
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream=stream)
     mats = [work[int(offs[q]):int(offs[q]) + sizes[q]] for q in range(len(specs))]
-    from paper_1709_06816_gb300 import autotune
     classes = autotune.apply(ctx, local)
     table, outs = ctx.make_jobs(mats, [n for n, _, _ in specs], [l for _, l, _ in specs])
     plan = native.lw_batch_create(ctx.handle, table)
@@ -420,6 +603,16 @@ def run_batched(args, local, plain_sample: int = 256):
     finally:
         native.lw_batch_destroy(plan)
     batch_ms = statistics.median(times)
+    # a sample of the jobs against the oracle
+    check = list(range(0, len(specs), 128))
+    bad = 0
+    for q in check:
+        D = pristine[int(offs[q]):int(offs[q]) + sizes[q]].cpu().numpy()
+        wm, wh, _, _ = oracle.cached(D, specs[q][0], specs[q][1])
+        m, h = outs[q]
+        if not (np.array_equal(m.cpu().numpy(), wm)
+                and np.array_equal(h.cpu().numpy().view(np.uint32), wh.view(np.uint32))):
+            bad += 1
     # plain path: one lw_cluster launch per job, same stream, a sample of the jobs
     pick = list(range(0, len(specs), max(1, len(specs) // plain_sample)))[:plain_sample]
     with torch.cuda.stream(stream):
@@ -439,6 +632,15 @@ def run_batched(args, local, plain_sample: int = 256):
     ctx.close()
     jobs_per_s = len(specs) / (batch_ms * 1e-3)
     plain_jobs_per_s = len(pick) / (plain_ms * 1e-3)
+    rec = work_counts("batch4096:mixed")
+    alg = 0
+    for n, link, _ in specs:
+        alg += algorithmic_bytes(n, link, {"rescan_cells": 0})[0]
+    note = "rescan and row-i terms missing"
+    if rec is not None:
+        alg += 4 * int(rec["rescan_cells"]) + 4 * int(rec.get("rowi_cells", 0))
+        note = "rescan and row-i terms from the oracle's runs of all 4096 jobs"
+    achieved = alg / (batch_ms * 1e-3) / 1e9
     return {
         "metric": "jobs/s (4096 independent jobs, n log-uniform in [64,2048], mixed linkage)",
         "value": jobs_per_s, "unit": "jobs/s", "ms_per_batch": batch_ms,
@@ -446,67 +648,139 @@ def run_batched(args, local, plain_sample: int = 256):
         "total_merges": total_merges, "matrix_bytes": 4 * int(sum(sizes)),
         "plain_jobs_per_s": plain_jobs_per_s, "plain_sample_jobs": len(pick),
         "speedup_vs_plain": jobs_per_s / plain_jobs_per_s,
+        "parity": {"oracle_checked_jobs": len(check), "mismatches": bad},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "algorithmic_bytes": alg, "algorithmic_note": note,
+                     "note": "the 4.98 GB of triangles exceed L2 together; each job alone fits L2"},
         "step": "restore all matrices (one device copy) + one batch-plan run (CUDA graph: "
                 "per size class, queue reset + persistent CTA-per-job kernel, classes side by side)",
         "classes": classes,
     }
 
 
-def run_serving(args, local, n_requests: int = 2000, bank_size: int = 48):
-    """The serving workload: a Poisson stream (mean 200 requests/s) of
-    clustering requests, n log-uniform in [256, 32768], linkage uniform over
-    the four, R^16 Gaussian-mixture distances, through a server with a
-    120 GB pool.  Matrices come from a bank of bank_size requests of the same
-    stream, generated on the device beforehand (request q uses bank entry
-    q mod bank_size, with that entry's n); latency runs from submission (the
-    matrix is ready on the device) to completion."""
-    import time as _time
+def run_serving(args, local):
+    """The serving workload: Poisson streams of clustering requests (n
+    log-uniform in [256, 32768], linkage uniform over the four, R^16
+    Gaussian-mixture distances) through a server with a 120 GB pool, at
+    several offered rates.  Each request's own matrix is generated on the
+    device on a side stream ahead of its arrival (a generator thread) and
+    submitted at its arrival time; latency runs from submission (matrix
+    ready) to completion.  The requests of the highest rate are then run
+    one by one through lw_cluster (the plain per-job path): their results
+    must match the served ones bit for bit, and their total time gives the
+    plain jobs/s."""
+    import queue
+    import threading
 
+    import numpy as np
     import torch
 
     import synth
+    from paper_1709_06816_gb300 import Context
     from paper_1709_06816_gb300.native import Server
 
     dev = f"cuda:{local}"
-    stream_specs = synth.serve_requests(n_requests)
-    bank = []
-    for (_, n, link, K, q) in stream_specs[:bank_size]:
-        rng_seed = [4, q]
-        pts = synth.gmm_points(__import__("numpy").random.default_rng(rng_seed), n, 16, K, 10.0, 1.0)
-        bank.append((synth.packed_distances(pts, device=dev), n, link))
-    outs = []
-    for q in range(n_requests):
-        D, n, link = bank[q % bank_size]
-        outs.append((torch.empty((n - 1, 2), dtype=torch.int32, device=dev),
-                     torch.empty(n - 1, dtype=torch.float32, device=dev)))
-    torch.cuda.synchronize()
-    srv = Server(local, budget_bytes=120 * 10**9, lanes=48)
+
+    def make(spec, gen_stream):
+        _, n, link, K, q = spec
+        pts = synth.gmm_points(np.random.default_rng([4, q]), n, 16, K, 10.0, 1.0)
+        with torch.cuda.stream(gen_stream):
+            D = synth.packed_distances(pts, device=dev)
+            ev = torch.cuda.Event()
+            ev.record(gen_stream)
+        return D, ev
+
+    def one_rate(rate, count):
+        specs = synth.serve_requests(count, rate=rate)
+        gen_stream = torch.cuda.Stream(device=dev)
+        ready = queue.Queue(maxsize=64)
+
+        def producer():
+            for spec in specs:
+                ready.put(make(spec, gen_stream))
+
+        th = threading.Thread(target=producer, daemon=True)
+        outs, live, late = [], {}, 0
+        srv = Server(local, budget_bytes=120 * 10**9, lanes=48)
+        try:
+            th.start()
+            t0 = time.perf_counter()
+            for q, spec in enumerate(specs):
+                D, ev = ready.get()
+                wait = spec[0] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                elif wait < -0.005:
+                    late += 1
+                ev.synchronize()
+                n, link = spec[1], spec[2]
+                m = torch.empty((n - 1, 2), dtype=torch.int32, device=dev)
+                h = torch.empty(n - 1, dtype=torch.float32, device=dev)
+                tk = srv.submit(D, n, link, m, h)
+                live[tk] = D
+                outs.append((tk, m, h))
+                if q % 16 == 0:  # free the matrices of finished requests
+                    for t in [t for t in live if srv.poll(t)[0]]:
+                        del live[t]
+            submit_s = time.perf_counter() - t0
+            rc = srv.drain()
+            st = srv.stats()
+        finally:
+            srv.close()
+            th.join()
+        live.clear()
+        return specs, outs, st, rc, submit_s, late
+
+    rates = (25, 50, 100, 200)
+    results = []
+    last = None
+    for rate in rates:
+        count = max(100, int(rate * args.serve_seconds))
+        specs, outs, st, rc, submit_s, late = one_rate(rate, count)
+        merges = sum(s[1] - 1 for s in specs)
+        results.append({
+            "offered_rate": count / specs[-1][0], "requests": count, "completed": st["completed"],
+            "failed": st["failed"], "jobs_per_s": st["completed"] / st["wall_s"] if st["wall_s"] else None,
+            "merges_per_s": merges / st["wall_s"] if st["wall_s"] else None,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "peak_inflight": st["peak_inflight"], "peak_pool_bytes": st["peak_bytes"],
+            "arrivals_late": late, "status": rc})
+        last = (specs, outs)
+        torch.cuda.empty_cache()
+    # the plain path on the last (highest) rate's requests: alone, one by one
+    specs, outs = last
+    ctx = Context(local)
+    gen_stream = torch.cuda.Stream(device=dev)
+    plain_ms, same = 0.0, 0
     try:
-        t0 = _time.perf_counter()
-        for q, (arrival, _, _, _, _) in enumerate(stream_specs):
-            wait = arrival - (_time.perf_counter() - t0)
-            if wait > 0:
-                _time.sleep(wait)
-            D, n, link = bank[q % bank_size]
-            m, h = outs[q]
-            srv.submit(D, n, link, m, h)
-        submit_s = _time.perf_counter() - t0
-        rc = srv.drain()
-        st = srv.stats()
+        for spec, (_, m, h) in zip(specs, outs):
+            D, ev = make(spec, gen_stream)
+            ev.synchronize()
+            n, link = spec[1], spec[2]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pm, ph = ctx.cluster(D, n, link)
+            e1.record()
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            same += bool(torch.equal(pm, m) and torch.equal(ph.view(torch.int32), h.view(torch.int32)))
+            del D
     finally:
-        srv.close()
-    merges = sum(bank[q % bank_size][1] - 1 for q in range(n_requests))
+        ctx.close()
+    plain_jobs_per_s = len(specs) / (plain_ms * 1e-3)
+    top = results[-1]
+    sustained = [r for r in results if r["p99_ms"] is not None and r["arrivals_late"] == 0
+                 and r["jobs_per_s"] and r["jobs_per_s"] >= 0.9 * r["offered_rate"]]
     return {
-        "metric": "served jobs/s and latency (Poisson 200 req/s, n log-uniform [256, 32768])",
-        "value": st["completed"] / st["wall_s"] if st["wall_s"] else None, "unit": "jobs/s",
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-        "requests": n_requests, "completed": st["completed"], "failed": st["failed"],
-        "offered_rate": n_requests / stream_specs[-1][0], "arrival_span_s": stream_specs[-1][0],
-        "submit_span_s": submit_s, "wall_s": st["wall_s"],
-        "merges_per_s": merges / st["wall_s"] if st["wall_s"] else None,
-        "peak_inflight": st["peak_inflight"], "peak_pool_bytes": st["peak_bytes"],
-        "pool_bytes": st["budget_bytes"], "lanes": 48, "status": rc,
-        "inputs": f"bank of {bank_size} matrices of the same request stream, generated on the device",
+        "metric": "served jobs/s and latency (Poisson arrivals, n log-uniform [256, 32768], mixed linkage)",
+        "value": top["jobs_per_s"], "unit": "jobs/s", "rates": results,
+        "sustained_rate": max((r["offered_rate"] for r in sustained), default=None),
+        "plain_jobs_per_s": plain_jobs_per_s,
+        "speedup_vs_plain": top["jobs_per_s"] / plain_jobs_per_s if top["jobs_per_s"] else None,
+        "plain_matches_served": same, "plain_checked": len(specs),
+        "pool_bytes": 120 * 10**9, "lanes": 48,
+        "inputs": "each request's own matrix, generated on the device ahead of its arrival",
     }
 
 
@@ -514,7 +788,7 @@ def run_reference(args, world, rank, local):
     """The reference arm: the CPU oracle, each step a bounded sample."""
     if rank != 0:
         return
-    import numpy as np
+    import numpy as np  # noqa: F401
     import torch
 
     import oracle
@@ -522,32 +796,29 @@ def run_reference(args, world, rank, local):
 
     w = synth.workload(args.workload)
     n = w.n
-    if torch.cuda.is_available():
-        D_host = w.matrix(device=f"cuda:{local}").cpu().numpy()
-        torch.cuda.empty_cache()
-    else:
+    if not torch.cuda.is_available():
         print(json.dumps({"impl": "reference", "unavailable":
                           "the n=65536 conformer matrix is generated on the GPU; none visible"}))
         return
+    D_host = w.matrix(device=f"cuda:{local}").cpu().numpy()
+    torch.cuda.empty_cache()
     oracle.build()
-    rates = []
-    infos = []
+    key = f"{args.workload}:{LINKAGE}"
+    rates, infos = [], []
     for k in range(args.warmup + args.steps):
-        rate, info = oracle_sample(D_host, n, LINKAGE, target_s=args.ref_step_seconds)
+        rate, info = oracle_rate(D_host, n, LINKAGE, key, args.ref_step_seconds)
         if k >= args.warmup:
             rates.append(rate)
             infos.append(info)
     value = statistics.median(rates)
-    est = statistics.median(i["est_total_s"] for i in infos)
-    sample = (f"each step: init + first ~{infos[0]['K']} of {n - 1} merges of the n={n} matrix on "
-              f"{infos[0]['cores']} host threads; full-run time extrapolated by work sum(m_t)")
+    wall_ms = 1e3 * statistics.mean(i["wall_s"] for i in infos)
+    sample = ("each step: " + cpu_sample_text(infos[0], n)
+              + "; value = median over the steps; ms_per_step = measured wall time of one step")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": wall_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "linkage": "complete",
-                   "l2": "inputs larger than L2 (8.59 GB packed triangle)",
-                   "parallelism": "host cores (OpenMP)"},
+        "config": bench_config(n, world),
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
                          "cores": infos[0]["cores"], "sample": sample},
@@ -558,23 +829,28 @@ def run_reference(args, world, rank, local):
 
 def run_cta_sweep(args, local):
     """Time of one clustering against the number of CTAs (the GPU analogue of
-    the paper's running time against processor count, Section 6), at the
-    paper's mean problem size n = 1968 (conformer-like chains), complete
-    linkage.  Prints one JSON line; every point is the best of five runs of
-    a synchronised lw_cluster call (host wall clock, launch included)."""
+    the paper's running time against processor count, Section 6, Figure 2),
+    at the paper's mean problem size n = 1968 (conformer-like chains),
+    complete linkage.  Every point is the best of five synchronised
+    lw_cluster calls (host wall clock, launch included) and its result is
+    compared with the oracle's."""
+    import numpy as np
     import torch
+
+    import oracle
     import synth
     from paper_1709_06816_gb300 import Context
     torch.cuda.set_device(local)
     w = synth.workload(f"conformer{args.sweep_n}")
-    src = w.matrix(device=f"cuda:{local}")
+    D = w.matrix()
+    want_m, want_h, _, _ = oracle.cached(D, w.n, LINKAGE)
+    src = torch.from_numpy(D).to(f"cuda:{local}")
     work = src.clone()
     ctx = Context(local)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     blocks = (w.n + 31) // 32  # a grid holds at most one CTA per 32-row block
     grids = sorted({min(g, sms, blocks) for g in (1, 2, 4, 8, 16, 32, 64, 128, sms)})
     points = []
-    ref = None
     for g in grids:
         ctx.set_grid(g)
         best = float("inf")
@@ -585,12 +861,13 @@ def run_cta_sweep(args, local):
             m, h = ctx.cluster(work, w.n, LINKAGE)
             torch.cuda.synchronize()
             best = min(best, time.perf_counter() - t0)
-        got = (m.cpu().numpy().tobytes(), h.cpu().numpy().tobytes())
-        ref = ref or got
-        points.append({"ctas": ctx.stats()["grid"], "ms": best * 1e3, "same_result": got == ref})
+        ok = bool(np.array_equal(m.cpu().numpy(), want_m)
+                  and np.array_equal(h.cpu().numpy().view(np.uint32), want_h.view(np.uint32)))
+        points.append({"ctas_requested": g, "ctas": ctx.stats()["grid"], "ms": best * 1e3,
+                       "oracle_match": ok})
     ctx.close()
-    print(json.dumps({"experiment": "clustering time vs CTAs", "n": w.n, "linkage": "complete",
-                      "data": "synthetic conformer-like chains", "points": points}), flush=True)
+    return {"experiment": "clustering time vs CTAs (Section 6, Figure 2 analogue)", "n": w.n,
+            "linkage": LINK_NAMES[LINKAGE], "data": "synthetic conformer-like chains", "points": points}
 
 
 def main(argv=None):
@@ -601,13 +878,17 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target length of the CPU oracle sample")
-    ap.add_argument("--ref-step-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival span of each offered rate of the serving workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other single-matrix workloads")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the CTA-count sweep")
     ap.add_argument("--cta-sweep", action="store_true",
-                    help="instead of the benchmark: clustering time against the CTA count")
+                    help="only the clustering time against the CTA count")
     ap.add_argument("--sweep-n", type=int, default=1968)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload name (profiling uses smaller conformer<N> cases)")
@@ -630,7 +911,7 @@ def main(argv=None):
             __graft_entry__.build()
             if args.cta_sweep:
                 if rank == 0:
-                    run_cta_sweep(args, local)
+                    print(json.dumps(run_cta_sweep(args, local)), flush=True)
             else:
                 run_ours(args, world, rank, local)
     finally:

@@ -66,7 +66,8 @@ typedef enum {
     LW_ERR_OOM = 3,           /* device or host allocation failed */
     LW_ERR_CUDA = 4,          /* a CUDA runtime call failed (see lw_last_error) */
     LW_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
-    LW_ERR_BUSY = 6           /* the context is in use by another call */
+    LW_ERR_BUSY = 6,          /* the context is in use by another call */
+    LW_ERR_CANCELLED = 7      /* a served request was cancelled before it ran */
 } lw_status;
 
 /* Largest n accepted: cluster sizes stay exact in FP32 and packed indices
@@ -143,12 +144,13 @@ lw_status lw_wait(lw_ctx *ctx);
  *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish;
  *   [14] rows rescanned at once by their owner (cache emptied),
  *   [15] live cells read by those rescans,
- *   [16..23] with LW_OPT_PHASE_TIMES on, a finer split of [9], [12] and
- *       [13] (same units): [16] reading the CTAs' records, [17] the walk
- *       and refill installs, [18] the chain's sizes, stamps and member
+ *   [16..25] with LW_OPT_PHASE_TIMES on, a finer split of [9], [11], [12]
+ *       and [13] (same units): [16] reading the CTAs' records, [17] the
+ *       walk and refill installs, [18] the chain's sizes, stamps and member
  *       cells, [19] the cross-CTA minima of the new cells, [20] the
  *       certification, [21] bookkeeping and survivor caches, [22] pass 2,
- *       [23] owner rescans.
+ *       [23] owner rescans; refill scans in the row-log layout: [24] the
+ *       log part, [25] the matrix part; [26] the walk alone (part of [17]).
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 
@@ -163,7 +165,7 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *                     so the other CTAs' bounded waits run out and the call
  *                     reports LW_ERR_TIMEOUT with the context still usable;
  *                     -1 switches it off (the default);
- *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..13]);
+ *   LW_OPT_PHASE_TIMES  1: accumulate per-phase time (lw_get_stats [8..23]);
  *   LW_OPT_BATCH_SPLIT  largest n a batch runs on a single CTA (0: the
  *                     largest that fits one CTA's shared memory); larger
  *                     jobs of a batch run over the whole device;
@@ -179,7 +181,12 @@ lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
  *                     triangle), so that every merge moves contiguous words;
  *                     2 the packed triangle (dist itself, no extra memory).
  *                     One-CTA runs always use the packed triangle.  Results
- *                     are the same either way.
+ *                     are the same either way;
+ *   LW_OPT_TEST_FAIL_ALLOC  failure-injection test hook: the next `value`
+ *                     device allocations of the context (workspace, matrix
+ *                     copy, working layout, batch plans) fail on the host,
+ *                     before cudaMalloc is called; the call reports
+ *                     LW_ERR_OOM and the context stays usable.
  * Returns LW_ERR_INVALID_ARG for an unknown option or value.
  */
 enum {
@@ -189,7 +196,8 @@ enum {
     LW_OPT_PHASE_TIMES = 4,
     LW_OPT_BATCH_SPLIT = 5,
     LW_OPT_CTA_THREADS = 6,
-    LW_OPT_LAYOUT = 7
+    LW_OPT_LAYOUT = 7,
+    LW_OPT_TEST_FAIL_ALLOC = 8
 };
 lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
 
@@ -202,20 +210,22 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value);
  * memory pool or arena that owns every allocation, inside a host
  * application's plug-in, or in a loop that must never enter the allocator.
  * It needs no lw_ctx and allocates nothing, host or device: the kernel's
- * scratch (cluster sizes, exchange records, barrier words) is a fixed
- * file-scope device array of 2 MB in liblw.so, created when the library is
- * loaded on a device and held by every device that loads it until the
- * process exits.
+ * global scratch (cluster sizes, exchange records, refill lists, barrier
+ * words) is a fixed file-scope device array of 2 MB in liblw.so.  The array
+ * exists on a device from the moment the library's device code is loaded
+ * there -- with CUDA's lazy module loading that is the first call on that
+ * device -- and is held until the process exits.  The working matrix is the
+ * caller's packed triangle.
  *   dist, merges_out, heights_out  DEVICE pointers as for lw_cluster (dist is
  *                overwritten in place); n <= LW_NOALLOC_MAX_N.
  *   cuda_stream  stream to run on (NULL: the legacy default stream); the call
  *                blocks until the run is finished.
- * The first call on each device looks up the scratch address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  All calls share the one scratch array,
- * which keeps the last call's contents (each call clears what must start
- * zeroed), so calls that overlap on the GPU -- from several host threads or
- * streams at once -- race and must be serialised by the caller.
+ * Each call looks up the scratch address (cudaGetSymbolAddress) with the
+ * current device; the first call on a device also loads the module, so make
+ * it before any stream capture begins.  All calls share the one scratch
+ * array, which keeps the last call's contents (each call clears what must
+ * start zeroed), so calls that overlap on the GPU -- from several host
+ * threads or streams at once -- race and must be serialised by the caller.
  * Errors: LW_ERR_INVALID_ARG for n > LW_NOALLOC_MAX_N, a bad linkage or a
  * pointer that is not device memory; LW_ERR_INVALID_INPUT, LW_ERR_TIMEOUT
  * and LW_ERR_CUDA as for lw_cluster.
@@ -304,7 +314,7 @@ typedef struct lw_server_stats {
     int64_t peak_bytes;    /* largest sum of footprints admitted at once */
     int64_t budget_bytes;  /* the pool size */
     int32_t peak_inflight; /* most requests admitted at once */
-    int32_t pad;
+    int32_t cancelled;     /* requests cancelled while queued */
     double p50_ms, p99_ms, mean_ms; /* latency, submission to completion */
     double wall_s;         /* first submission to last completion */
 } lw_server_stats;
@@ -327,8 +337,15 @@ lw_status lw_server_submit(lw_server *srv, const float *dist, int64_t n, int lin
 lw_status lw_server_poll(lw_server *srv, uint64_t ticket, int32_t *done, lw_status *status,
                          double *latency_ms);
 
+/* lw_server_cancel -- withdraw a request that is still queued: it never
+ * runs, and lw_server_poll reports it done with LW_ERR_CANCELLED.  Returns
+ * LW_ERR_BUSY if the request was admitted already (it runs to the end) and
+ * LW_ERR_INVALID_ARG for an unknown ticket.  (Not a step of the paper: a
+ * service of the request loop.) */
+lw_status lw_server_cancel(lw_server *srv, uint64_t ticket);
+
 /* lw_server_drain -- block until every submitted request finished; returns
- * LW_OK if all succeeded. */
+ * LW_OK if all succeeded (cancelled requests do not count as failures). */
 lw_status lw_server_drain(lw_server *srv);
 
 /* lw_server_get_stats -- counters, latency percentiles and wall time. */

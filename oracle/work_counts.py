@@ -17,7 +17,7 @@ Finally it times ``oracle.sample`` (the bounded prefix the benchmark's CPU
 baseline runs) on the same matrix, so the benchmark can calibrate the
 prefix's extrapolated time against this full run.
 
-    python -m oracle.work_counts conformer65536:1 [name:linkage ...]
+    python -m oracle.work_counts conformer65536:1 [name:linkage ...] [batch4096:mixed]
 
 generates each workload with ``synth`` (on the GPU when torch sees one,
 else with numpy), runs ``oracle.cached`` over all merges on the host cores
@@ -43,6 +43,22 @@ def sha256(a) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
+def batch_counts(oracle, synth) -> dict:
+    """The batched workload (synth.batch_jobs(): 4096 jobs, mixed linkage):
+    the oracle's counters summed over every job."""
+    t0 = time.time()
+    tot = {"jobs": 0, "rescan_cells": 0, "rescans": 0, "rowi_cells": 0, "updated": 0, "sum_m": 0}
+    for q, spec in enumerate(synth.batch_jobs()):
+        n, link, _ = spec
+        _, _, st, _ = oracle.cached(synth.job_matrix(spec, q), n, link, inplace=True)
+        tot["jobs"] += 1
+        for k in ("rescan_cells", "rescans", "rowi_cells", "updated", "sum_m"):
+            tot[k] += st[k]
+    tot["oracle_seconds"] = round(time.time() - t0, 1)
+    tot["oracle_threads"] = oracle.threads()
+    return tot
+
+
 def main(argv):
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
@@ -58,6 +74,10 @@ def main(argv):
         table = {}
     for item in argv:
         name, link = item.split(":")
+        if name == "batch4096":
+            table[item] = batch_counts(oracle, synth)
+            print(item, table[item], flush=True)
+            continue
         link = int(link)
         w = synth.workload(name)
         try:

@@ -25,6 +25,7 @@ struct lw_ctx {
     int layout_opt = 0;              // 0 automatic, 1 row-log layout, 2 packed triangle
     long long timeout_ms = 5000;
     int test_skip_arrive = -1;
+    long long test_fail_alloc = 0;  // the next this many device allocations fail (test hook)
     int phase_timing = 0;
     long long batch_split = 0;  // 0: largest n one CTA can hold
     std::vector<std::pair<long long, int>> batch_classes;  // (n_hi, CTA threads)
@@ -88,10 +89,24 @@ bool is_device_ptr(const void *p)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Failure-injection hook (LW_OPT_TEST_FAIL_ALLOC): consumes one injected
+// allocation failure, if any is pending.  The failure is made on the host,
+// before cudaMalloc is called.
+bool injected_alloc_failure(lw_ctx *ctx, const char *what)
+{
+    if (ctx->test_fail_alloc <= 0)
+        return false;
+    --ctx->test_fail_alloc;
+    set_err(ctx, "allocation for %s failed (injected by LW_OPT_TEST_FAIL_ALLOC)", what);
+    return true;
+}
+
 lw_status ensure(lw_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what)
 {
     if (*cap >= need)
         return LW_OK;
+    if (injected_alloc_failure(ctx, what))
+        return LW_ERR_OOM;
     if (*buf) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess)
@@ -492,6 +507,11 @@ lw_status lw_set_option(lw_ctx *ctx, int option, int64_t value)
     case LW_OPT_PHASE_TIMES:
         ctx->phase_timing = value != 0;
         return LW_OK;
+    case LW_OPT_TEST_FAIL_ALLOC:
+        if (value < 0)
+            return LW_ERR_INVALID_ARG;
+        ctx->test_fail_alloc = value;
+        return LW_OK;
     case LW_OPT_LAYOUT:
         if (value < 0 || value > 2)
             return LW_ERR_INVALID_ARG;
@@ -663,6 +683,10 @@ lw_status lw_batch_create(lw_ctx *ctx, const lw_job *jobs, int32_t njobs, lw_bat
     auto alloc = [&](void **pp, size_t bytes, const char *what) {
         if (st != LW_OK)
             return;
+        if (injected_alloc_failure(ctx, what)) {
+            st = LW_ERR_OOM;
+            return;
+        }
         cudaError_t ee = cudaMalloc(pp, bytes < 16 ? 16 : bytes);
         if (ee != cudaSuccess) {
             cudaGetLastError();
@@ -868,6 +892,7 @@ const char *lw_status_string(lw_status s)
     case LW_ERR_CUDA: return "CUDA error";
     case LW_ERR_TIMEOUT: return "device wait timed out";
     case LW_ERR_BUSY: return "context busy";
+    case LW_ERR_CANCELLED: return "request cancelled";
     }
     return "unknown status";
 }

@@ -312,10 +312,12 @@ struct Shared {
     int si[S], sj[S];            // row-log layout: the members' stamps before the round
     u64 wam[W][S], whm[W][S];    // per warp: smallest new cell per pair (all k, k > i)
     u64 gamin[S], ghmin[S];      // the same over all CTAs
-    float Dm[2 * S][2 * S];      // D between members (2a = i_a, 2a + 1 = j_a)
-    float X[S][S];               // cell (i_a, i_b) after merge a alone
-    float Y[S][S];               // cell (i_a, j_b) after merge a alone
-    float C[S][S];               // cell (i_a, i_b) after merges a then b (a < b)
+    // (rows padded by one word: the certification reads a column of these
+    // per warp, one row per lane, which would otherwise hit a single bank)
+    float Dm[2 * S][2 * S + 1];  // D between members (2a = i_a, 2a + 1 = j_a)
+    float X[S][S + 1];           // cell (i_a, i_b) after merge a alone
+    float Y[S][S + 1];           // cell (i_a, j_b) after merge a alone
+    float C[S][S + 1];           // cell (i_a, i_b) after merges a then b (a < b)
     // the previous round's merges, replayed on installed refills
     int ppi[S], ppj[S];
     int nprev;
@@ -466,10 +468,12 @@ __device__ __forceinline__ void init_cell(float v, long long q, unsigned c, cons
             return;
         }
     }
-    // cells above the list's largest value cannot enter it
-    if (u > (unsigned)(L[K - 1] >> 32))
+    // a key not below the list's largest cannot enter it (an exact test of
+    // the whole key: cells tying on the value are common and go no further)
+    const u64 key = ((u64)u << 32) | (u64)c;
+    if (key >= L[K - 1])
         return;
-    list_insert(L, ((u64)u << 32) | (u64)c);
+    list_insert(L, key);
 }
 
 // K smallest keys of row r (all columns are live at launch), computed by one
@@ -524,8 +528,11 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
 // K smallest keys of row r over live columns, computed by the whole CTA (a
 // refill, or a row whose cache emptied).  Adds the live cells read to
 // `live_cells`.  Result in sh.tko.
+// (Row scans are kept out of line: inside the round loop's register
+// allocation their loads in flight would be spilled.)
 template <int NT, int S>
-__device__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap, Shared<NT, S> &sh,
+__device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap,
+                                            Shared<NT, S> &sh,
                                long long &live_cells)
 {
     const long long n = p.n;
@@ -541,8 +548,9 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
         const long long c = q + base_c;
         if (live(bitmap, c)) {
             ++cnt;
-            if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
-                list_insert(L, make_key(v, (unsigned)c));
+            const u64 key = make_key(v, (unsigned)c);
+            if (key < L[K - 1])  // the whole key: ties on the value stop here
+                list_insert(L, key);
         }
     };
     // unaligned head and tail one word per thread; the body as 16-byte loads,
@@ -589,10 +597,13 @@ __device__ void block_row_topk(const MergeParams &p, long long r, const unsigned
 // own pass 2) take their survivors from the round's chain in shared memory,
 // older ones from the merge list.  Result in sh.tko.
 template <int NT, int S>
-__device__ void block_row_topk_log(const MergeParams &p, long long r, const unsigned *bitmap,
+__device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long r, const unsigned *bitmap,
                                    const unsigned *vpos, unsigned *newer, Shared<NT, S> &sh, long long t0,
-                                   int L0, long long &live_cells)
+                                   int L0, long long &live_cells, u64 *tlog = nullptr)
 {
+    // with phase timing on, thread 0 adds the time of the log part to
+    // tlog[0] and of the matrix part (and the top-K) to tlog[1]
+    u64 tm0 = tlog && threadIdx.x == 0 ? global_ns() : 0;
     const long long n = p.n;
     const long long nwords = (n + 31) / 32;
     const int sr = __ldcg(p.stamp + r);
@@ -603,8 +614,9 @@ __device__ void block_row_topk_log(const MergeParams &p, long long r, const unsi
     long long cnt = 0;
     auto take = [&](float v, long long c) {
         ++cnt;
-        if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
-            list_insert(L, make_key(v, (unsigned)c));
+        const u64 key = make_key(v, (unsigned)c);
+        if (key < L[K - 1])  // the whole key: ties on the value stop here
+            list_insert(L, key);
     };
     for (long long w = threadIdx.x; w < nwords; w += NT)
         newer[w] = 0u;
@@ -637,6 +649,11 @@ __device__ void block_row_topk_log(const MergeParams &p, long long r, const unsi
         }
     }
     __syncthreads();
+    if (tlog && threadIdx.x == 0) {
+        const u64 now = global_ns();
+        tlog[0] += now - tm0;
+        tm0 = now;
+    }
     // (b) row r of M at live columns c > r not found in the log: 16-byte
     // pieces (rows start 16-byte aligned), eight in flight per thread
     const float *row = p.D + r * p.pitch;
@@ -682,12 +699,15 @@ __device__ void block_row_topk_log(const MergeParams &p, long long r, const unsi
     }
     live_cells += cnt;
     block_topk(L, sh);
+    if (tlog && threadIdx.x == 0)
+        tlog[1] += global_ns() - tm0;
 }
 
 // K smallest keys of row r over live columns, computed by one warp (the
 // rows of a one-CTA job are refreshed this way, several warps side by side).
 // Adds the live cells read to `live_cells`.  Result in out (all lanes).
-__device__ void warp_row_refresh(const MergeParams &p, long long r, const unsigned *bitmap, u64 (&out)[K],
+__device__ __noinline__ void warp_row_refresh(const MergeParams &p, long long r, const unsigned *bitmap,
+                                              u64 (&out)[K],
                                  long long &live_cells)
 {
     const int lane = threadIdx.x & 31;
@@ -703,8 +723,9 @@ __device__ void warp_row_refresh(const MergeParams &p, long long r, const unsign
         const long long c = q + base_c;
         if (live(bitmap, c)) {
             ++cnt;
-            if (__float_as_uint(v) <= (unsigned)(L[K - 1] >> 32))
-                list_insert(L, make_key(v, (unsigned)c));
+            const u64 key = make_key(v, (unsigned)c);
+            if (key < L[K - 1])  // the whole key: ties on the value stop here
+                list_insert(L, key);
         }
     };
     long long a0 = p.aligned16 ? ((start + 3) & ~3LL) : end;
@@ -828,6 +849,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     // (certification) + xs5 (bookkeeping, survivor caches); ph5 = xs6 (pass 2)
     // + xs7 (owner rescans) + the publish
     u64 xs0 = 0, xs1 = 0, xs2 = 0, xs3 = 0, xs4 = 0, xs5 = 0, xs6 = 0, xs7 = 0;
+    u64 xscan[2] = {0, 0};  // refill scans in the row-log layout: log part, matrix part
+    u64 xwalk = 0;          // the walk itself (warp 0)
     u64 tmark = 0;
     auto lap = [&](u64 &acc) {
         if (p.timing && threadIdx.x == 0) {
@@ -1028,6 +1051,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             sh.nmyreq[par] = 0;
         lap(xs0);
 
+        const u64 twalk0 = p.timing && tid == 0 ? global_ns() : 0;
         if (warp == 0) {
             // ---- the walk: merge the G published lists in key order.  Lane
             // l keeps the heads of the lists of CTAs l, l + 32, ... in registers.
@@ -1116,6 +1140,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 sh.np = np;
                 sh.front = front;
             }
+            if (p.timing && tid == 0)
+                xwalk += global_ns() - twalk0;
         } else {
             // ---- refills served in the previous round: take the row's list,
             // then replay that round's merges (the scan ran before them, or
@@ -1482,7 +1508,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (rr < 0 || rr >= n - 1)
                     continue;  // the same for every thread of the CTA
                 if (p.full)
-                    block_row_topk_log(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells);
+                    block_row_topk_log(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells,
+                                       p.timing ? xscan : nullptr);
                 else
                     block_row_topk(p, rr, bitmap, sh, st_fill_cells);
                 if (tid < K / 2) {
@@ -1949,8 +1976,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 atomicAdd(St + 11, ph3);
                 atomicAdd(St + 12, ph4);
                 atomicAdd(St + 13, ph5);
-                const u64 xs[8] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7};
-                for (int q = 0; q < 8; ++q)
+                const u64 xs[11] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7, xscan[0], xscan[1], xwalk};
+                for (int q = 0; q < 11; ++q)
                     atomicAdd(St + 16 + q, xs[q]);
             }
         }

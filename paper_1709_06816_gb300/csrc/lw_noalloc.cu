@@ -6,49 +6,42 @@
 // mid-run), plug-ins inside a host application that owns all allocations,
 // and real-time loops that must not call the allocator at all.  This entry
 // point serves them: the caller passes its own device buffers for the
-// matrix and the outputs, and the kernel's scratch (row-minimum keys,
-// cluster sizes, exchange records, barrier and status words) lives in one
-// file-scope __device__ array of fixed size, allocated once when the library
-// is loaded on a device and kept until the process exits.
+// matrix and the outputs, and the kernel's global scratch (cluster sizes,
+// per-CTA exchange records and pair minima, refill lists, barrier, status
+// and counter words) lives in one file-scope __device__ array of fixed size.
+// The array comes into being on a device when the library's device code is
+// loaded there -- with CUDA's lazy module loading, during the first call on
+// that device -- and stays until the process exits.  The row caches live in
+// shared memory.  The working matrix is the caller's packed triangle (the
+// row-log layout would need memory of its own).
 //
 // Nothing here calls cudaMalloc, cudaFree, cudaMallocHost or any allocating
-// library routine.  The only set-up is cudaGetSymbolAddress on the first call
-// per device (see include/lw.h for the rules that follow from that).
+// library routine.  Each call looks the array's device address up with
+// cudaGetSymbolAddress (see include/lw.h for the rules that follow).
 
 #include "../../include/lw.h"
 #include "lw_internal.h"
 
-#include <mutex>
 
 namespace {
 
-// Largest n this entry point accepts and the scratch that serves it: cluster
-// sizes 4n, per-CTA records and refill lists (about 8.5 KB per CTA of a
-// full-device grid), barrier, status and stats words.
+// Largest n this entry point accepts and the scratch that serves it
+// (workspace_layout): cluster sizes 4n B; per CTA a 240 B record and 512 B of
+// pair minima; 16 KB of refill lists; barrier, status and counter words.  At
+// n = 16384 on a 256-CTA grid that is about 275 KB; the array holds 2 MB,
+// and every call checks its layout against that size.
 constexpr long long kNoAllocMaxN = LW_NOALLOC_MAX_N;
 constexpr size_t kScratchBytes = 2 * 1024 * 1024;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_scratch on the current device (first call per device
-// looks it up).  In host code `g_scratch` names a host-side stand-in, not
-// device memory, so it is never passed to a kernel directly.
-cudaError_t scratch_address(int device, void **out)
+// Device address of g_scratch on the current device.  In host code
+// `g_scratch` names a host-side stand-in, not device memory, so it is never
+// passed to a kernel directly.  The address is looked up on every call (it
+// allocates nothing, and stays right after a device reset reloads the module).
+cudaError_t scratch_address(void **out)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_scratch_ptr[device] = p;
-    }
-    *out = g_scratch_ptr[device];
-    return cudaSuccess;
+    return cudaGetSymbolAddress(out, g_scratch);
 }
 
 bool is_device_memory(const void *p)
@@ -74,7 +67,7 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
         !is_device_memory(merges_out) || !is_device_memory(heights_out))
         return LW_ERR_INVALID_ARG;
     int device = 0, num_sms = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices ||
+    if (cudaGetDevice(&device) != cudaSuccess ||
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
         return LW_ERR_CUDA;
@@ -93,7 +86,7 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
         return LW_ERR_INVALID_ARG;
 
     void *base = nullptr;
-    if (scratch_address(device, &base) != cudaSuccess) {
+    if (scratch_address(&base) != cudaSuccess) {
         cudaGetLastError();
         return LW_ERR_CUDA;
     }

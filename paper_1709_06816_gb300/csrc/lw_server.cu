@@ -9,10 +9,13 @@
 // while others are on the GPU start as soon as a lane and memory free up and
 // their work overlaps on the device.  A request that does not fit the pool at
 // the moment is passed over by smaller ones behind it (backfill); one that
-// can never fit is refused at submission.  The multi-CTA grids of the admitted
-// requests never add up to more CTAs than the device holds at once (one
-// 512-thread CTA per SM), so no two cooperative grids can each hold part of
-// the device while waiting for the rest.
+// can never fit is refused at submission.  Every admitted kernel fits on the
+// device at the same time as all the others in flight: a 512-thread CTA of
+// the merge kernel fills an SM's registers and a 256-thread one half of them,
+// and the admitted requests' CTAs never need more than the SMs there are.  So
+// a cooperative grid is always resident as a whole: no grid waits at its
+// barrier for CTAs that another grid, or a one-CTA job, keeps off the device.
+// A request still in the queue can be cancelled.
 //
 // Large requests run with a modest grid (one CTA per 1024 objects): a merge
 // of the persistent kernel is bound by barrier and memory latency far more
@@ -64,7 +67,7 @@ struct Lane {
     bool busy = false;
     Request req;
     size_t block = 0;         // pool offset
-    int ctas = 0;             // CTAs of the request's grid
+    int units = 0;            // half-SM units the request's CTAs hold
     int32_t *dm = nullptr;    // device outputs when the request's are host memory
     float *dh = nullptr;
     size_t out_cap = 0;       // merges capacity (in steps)
@@ -99,12 +102,12 @@ struct lw_server {
     std::unordered_map<uint64_t, Result> results;
     uint64_t next_ticket = 1;
     int inflight = 0;
-    int ctas_inflight = 0;  // CTAs of the admitted requests' grids
+    int units_inflight = 0;  // half-SM units held by the admitted requests' CTAs
     bool stop = false;
     std::thread worker;
 
     // statistics
-    int64_t submitted = 0, completed = 0, failed = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0;
     size_t peak_bytes = 0;
     int peak_inflight = 0;
     std::vector<double> latencies;
@@ -156,6 +159,10 @@ struct lw_server {
     }
 
     static int threads_for(int64_t n) { return n <= 512 ? 256 : 512; }
+
+    // Half-SM units the request's CTAs hold while it runs: two per 512-thread
+    // CTA (all of an SM's registers), one per 256-thread CTA.
+    int units_for(int64_t n) const { return grid_for(n) * (threads_for(n) == 512 ? 2 : 1); }
 
     // Launch request r on lane L (scheduler thread, mutex held).
     lw_status launch(Lane &L, const Request &r, size_t off)
@@ -222,8 +229,8 @@ struct lw_server {
         }
         L.busy = false;
         --inflight;
-        ctas_inflight -= L.ctas;
-        L.ctas = 0;
+        units_inflight -= L.units;
+        L.units = 0;
     }
 
     void loop()
@@ -254,11 +261,11 @@ struct lw_server {
                     }
                 if (!free_lane)
                     break;
-                // every admitted grid must fit the device at once: cooperative
-                // grids wait on each other only through their own barriers
-                const int g = it->n > 1 ? grid_for(it->n) : 0;
-                const int ctas = g > 1 ? g : 0;  // one-CTA grids need no co-residency
-                if (ctas_inflight + ctas > num_sms) {
+                // every admitted kernel must fit the device together with the
+                // others in flight, so that no cooperative grid is ever only
+                // partly resident
+                const int units = it->n > 1 ? units_for(it->n) : 0;
+                if (units_inflight + units > 2 * num_sms) {
                     ++it;
                     continue;
                 }
@@ -271,8 +278,8 @@ struct lw_server {
                 L.req = *it;
                 L.block = off;
                 L.busy = true;
-                L.ctas = ctas;
-                ctas_inflight += ctas;
+                L.units = units;
+                units_inflight += units;
                 ++inflight;
                 if (it->n > 1) {
                     resident += it->bytes;
@@ -390,6 +397,28 @@ lw_status lw_server_poll(lw_server *s, uint64_t ticket, int32_t *done, lw_status
     return LW_OK;
 }
 
+lw_status lw_server_cancel(lw_server *s, uint64_t ticket)
+{
+    if (!s)
+        return LW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto res = s->results.find(ticket);
+    if (res == s->results.end())
+        return LW_ERR_INVALID_ARG;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if (it->ticket != ticket)
+            continue;
+        const auto now = Clock::now();
+        res->second.done = true;
+        res->second.status = LW_ERR_CANCELLED;
+        res->second.latency_ms = std::chrono::duration<double, std::milli>(now - it->t_submit).count();
+        ++s->cancelled;
+        s->queue.erase(it);
+        return LW_OK;
+    }
+    return LW_ERR_BUSY;  // admitted already (running or finished)
+}
+
 lw_status lw_server_drain(lw_server *s)
 {
     if (!s)
@@ -417,6 +446,7 @@ lw_status lw_server_get_stats(lw_server *s, lw_server_stats *st)
     st->failed = s->failed;
     st->peak_bytes = (int64_t)s->peak_bytes;
     st->peak_inflight = s->peak_inflight;
+    st->cancelled = (int32_t)s->cancelled;
     st->budget_bytes = (int64_t)s->budget;
     std::vector<double> v = s->latencies;
     std::sort(v.begin(), v.end());

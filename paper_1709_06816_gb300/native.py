@@ -22,7 +22,7 @@ LW_SINGLE, LW_COMPLETE, LW_AVERAGE, LW_WARD, LW_WEIGHTED, LW_CENTROID = 0, 1, 2,
 LINKAGES = {"single": 0, "complete": 1, "average": 2, "ward": 3, "weighted": 4, "centroid": 5}
 LW_OPT_GRID, LW_OPT_TIMEOUT_MS = 1, 2
 STATUS = {0: "LW_OK", 1: "LW_ERR_INVALID_ARG", 2: "LW_ERR_INVALID_INPUT", 3: "LW_ERR_OOM",
-          4: "LW_ERR_CUDA", 5: "LW_ERR_TIMEOUT", 6: "LW_ERR_BUSY"}
+          4: "LW_ERR_CUDA", 5: "LW_ERR_TIMEOUT", 6: "LW_ERR_BUSY", 7: "LW_ERR_CANCELLED"}
 
 # every symbol include/lw.h declares
 EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_stats",
@@ -30,8 +30,10 @@ EXPORTS = ("lw_create", "lw_cluster", "lw_cluster_async", "lw_wait", "lw_get_sta
            "lw_batch_create", "lw_batch_run", "lw_batch_wait", "lw_batch_destroy",
            "lw_set_batch_classes",
            "lw_cluster_batch", "lw_server_create", "lw_server_submit", "lw_server_poll",
-           "lw_server_drain", "lw_server_get_stats", "lw_server_destroy", "lw_cluster_noalloc")
+           "lw_server_drain", "lw_server_get_stats", "lw_server_destroy", "lw_server_cancel",
+           "lw_cluster_noalloc")
 LW_OPT_PHASE_TIMES, LW_OPT_BATCH_SPLIT, LW_OPT_CTA_THREADS, LW_OPT_LAYOUT = 4, 5, 6, 7
+LW_OPT_TEST_FAIL_ALLOC = 8
 
 
 class LwServerStats(ctypes.Structure):
@@ -39,11 +41,11 @@ class LwServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("peak_inflight", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("cancelled", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class LwJob(ctypes.Structure):
@@ -117,6 +119,8 @@ def load(path: str = LIB_PATH):
         lib.lw_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         lib.lw_server_poll.restype = ctypes.c_int
+        lib.lw_server_cancel.argtypes = [vp, ctypes.c_uint64]
+        lib.lw_server_cancel.restype = ctypes.c_int
         lib.lw_server_drain.argtypes = [vp]
         lib.lw_server_drain.restype = ctypes.c_int
         lib.lw_server_get_stats.argtypes = [vp, ctypes.POINTER(LwServerStats)]
@@ -177,8 +181,8 @@ def lw_wait(ctx: int) -> None:
 
 def lw_get_stats(ctx: int) -> dict:
     lib = load()
-    a = (ctypes.c_int64 * 24)()
-    s = lib.lw_get_stats(ctx, a, 24)
+    a = (ctypes.c_int64 * 27)()
+    s = lib.lw_get_stats(ctx, a, 27)
     if s != 0:
         raise LwError(s, "lw_get_stats")
     out = {"rounds": a[0], "idle_rounds": a[1], "updated": a[2], "grid": a[3],
@@ -189,7 +193,7 @@ def lw_get_stats(ctx: int) -> dict:
         names = ("barrier", "walk", "pass1", "refill", "certify", "pass2")
         out["phase_ms"] = {nm: a[8 + q] / G / 1e6 for q, nm in enumerate(names)}
         sub = ("records", "walk_installs", "chain", "minima", "certify", "bookkeeping", "pass2",
-               "rescans")
+               "rescans", "scan_log", "scan_matrix", "walk_only")
         out["subphase_ms"] = {nm: a[16 + q] / G / 1e6 for q, nm in enumerate(sub)}
     return out
 
@@ -277,6 +281,10 @@ class Server:
         if s != 0:
             raise LwError(s, "lw_server_poll")
         return bool(d.value), st.value, lat.value
+
+    def cancel(self, ticket: int) -> int:
+        """lw_server_cancel: 0 if the queued request was withdrawn, else its status code."""
+        return int(load().lw_server_cancel(self.handle, ticket))
 
     def drain(self) -> int:
         return int(load().lw_server_drain(self.handle))

@@ -215,6 +215,9 @@ def workload(name: str) -> Workload:
     * ``conformer65536``: n=65536 conformer-like chains (64 seed chains of 128
       beads, step 3.8, noise 0.5), d = ||delta|| / sqrt(128), seed 2;
       complete and Ward.
+    * ``serve<N>``: N points in R^16 from 16 isotropic Gaussians (centers
+      U[-10,10]^16, sigma=1), seed 4: one request of the serving stream's
+      recipe at a chosen size.
     Smaller ``conformer<N>`` / ``gmm<N>`` variants use the same recipes.
     """
     if name == "gmm512":
@@ -235,6 +238,12 @@ def workload(name: str) -> Workload:
                         "d=||delta||/sqrt(128), seed 2",
                         lambda rng: conformer_points(rng, n),
                         math.sqrt(128.0), None)
+    if name.startswith("serve"):
+        n = int(name[len("serve"):])
+        return Workload(name, n, (SINGLE, COMPLETE, AVERAGE, WARD), 4,
+                        f"{n} points in R^16, 16 isotropic Gaussians (centers U[-10,10]^16, sigma=1), "
+                        "the serving stream's recipe, seed 4",
+                        lambda rng: gmm_points(rng, n, 16, 16, 10.0, 1.0))
     if name.startswith("gmm"):
         n = int(name[3:])
         return Workload(name, n, (COMPLETE,), 0,

@@ -14,6 +14,8 @@ def test_algorithmic_bytes_terms():
     assert b == base and "missing" in note
     b, _ = bench.algorithmic_bytes(n, 1, {"rescan_cells": 7})
     assert b == base + 28
+    b, _ = bench.algorithmic_bytes(n, 1, {"rescan_cells": 7, "rowi_cells": 5})
+    assert b == base + 28 + 20  # the merged rows' recomputed minima
     b, _ = bench.algorithmic_bytes(n, 3, {"rescan_cells": 0})
     assert b == base + 4 * sum_m  # Ward also reads the sizes
 

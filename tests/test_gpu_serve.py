@@ -112,3 +112,78 @@ def test_arrivals_while_busy_and_refusal():
         assert e.value.status == 1
     finally:
         srv.close()
+
+
+def test_cancel_a_queued_request():
+    """A request still in the queue can be withdrawn: it never runs, polls as
+    done with LW_ERR_CANCELLED, and the others complete as usual; a request
+    that is running (or done) cannot be cancelled."""
+    reqs = _requests(12, 3, n_lo=1500, n_hi=2500)
+    srv = Server(0, budget_bytes=64 << 20, lanes=1)  # one lane: the rest wait in the queue
+    try:
+        outs, tickets = [], []
+        for D, n, link in reqs:
+            Dx = torch.from_numpy(D).cuda()
+            m = torch.empty((n - 1, 2), dtype=torch.int32, device="cuda")
+            h = torch.empty(n - 1, dtype=torch.float32, device="cuda")
+            outs.append((Dx, m, h))
+        torch.cuda.synchronize()
+        for (Dx, m, h), (D, n, link) in zip(outs, reqs):
+            tickets.append(srv.submit(Dx, n, link, m, h))
+        cancelled = [t for t in tickets[-4:] if srv.cancel(t) == 0]
+        assert len(cancelled) >= 3  # at most the first of them can have started
+        assert srv.drain() == 0
+        st = srv.stats()
+        assert st["cancelled"] == len(cancelled)
+        assert st["completed"] == len(reqs) - len(cancelled)
+        for t, (D, n, link), (_, m, h) in zip(tickets, reqs, outs):
+            done, status, _ = srv.poll(t)
+            assert done
+            if t in cancelled:
+                assert status == 7
+                continue
+            assert status == 0
+            am, ah = _alone(D, n, link)
+            assert np.array_equal(m.cpu().numpy(), am)
+            assert np.array_equal(_bits(h.cpu().numpy()), _bits(ah))
+        assert srv.cancel(tickets[0]) == 6  # finished: nothing to withdraw
+        assert srv.cancel(10**9) == 1       # unknown ticket
+    finally:
+        srv.close()
+
+
+def test_largest_request_size_matches_the_oracle():
+    """One request of the serving stream's largest size (n = 32768, the
+    stream's recipe: R^16, 16 Gaussians; group average) through the server,
+    next to smaller ones: the whole dendrogram equals the oracle's full run
+    (its stored digests, oracle/work_counts.py) bit for bit."""
+    import hashlib
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "bench_work_counts.json")) as f:
+        rec = json.load(f)["serve32768:2"]
+    w = synth.workload("serve32768")
+    D = w.matrix(device="cuda")
+    assert hashlib.sha256(D.cpu().numpy().tobytes()).hexdigest() == rec["input_sha256"]
+    m = torch.empty((w.n - 1, 2), dtype=torch.int32, device="cuda")
+    h = torch.empty(w.n - 1, dtype=torch.float32, device="cuda")
+    small = _requests(6, 4, n_lo=300, n_hi=3000)
+    srv = Server(0, budget_bytes=8 << 30, lanes=8)
+    try:
+        side = []
+        for Ds, n, link in small[:3]:
+            Dx = torch.from_numpy(Ds).cuda()
+            ms = torch.empty((n - 1, 2), dtype=torch.int32, device="cuda")
+            hs = torch.empty(n - 1, dtype=torch.float32, device="cuda")
+            side.append((Dx, ms, hs))
+        torch.cuda.synchronize()
+        for (Dx, ms, hs), (Ds, n, link) in zip(side, small):
+            srv.submit(Dx, n, link, ms, hs)
+        t = srv.submit(D, w.n, 2, m, h)
+        assert srv.drain() == 0
+        assert srv.poll(t)[:2] == (True, 0)
+    finally:
+        srv.close()
+    assert hashlib.sha256(m.cpu().numpy().tobytes()).hexdigest() == rec["merges_sha256"]
+    assert hashlib.sha256(h.cpu().numpy().tobytes()).hexdigest() == rec["heights_sha256"]

@@ -57,3 +57,4 @@ def test_uncertified_chain_is_caught():
         if not (np.array_equal(m, wm) and np.array_equal(_bits(h), _bits(wh))):
             caught += 1
     assert caught > 0
+

@@ -54,6 +54,36 @@ def test_noalloc_matches_lw_cluster_twice_in_a_row():
         assert np.array_equal(got[1].view(np.uint32), want[1].view(np.uint32)), (n, link)
 
 
+def test_noalloc_at_its_size_limit_matches_the_oracle():
+    """n = LW_NOALLOC_MAX_N (16384, a 512 MB triangle, every-SM grid): the
+    whole dendrogram equals the oracle's (its stored digest of the same
+    workload) and lw_cluster's, bit for bit."""
+    import hashlib
+    import json
+    import os
+    w = synth.workload("gmm16384q")
+    assert w.n == native.LW_NOALLOC_MAX_N
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "bench_work_counts.json")) as f:
+        rec = json.load(f)["gmm16384q:1"]
+    D = w.matrix(device="cuda")
+    keep = D.clone()
+    m = torch.empty((w.n - 1, 2), dtype=torch.int32, device="cuda")
+    h = torch.empty(w.n - 1, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    native.lw_cluster_noalloc(D, w.n, 1, m, h)
+    gm, gh = m.cpu().numpy(), h.cpu().numpy()
+    assert hashlib.sha256(gm.tobytes()).hexdigest() == rec["merges_sha256"]
+    assert hashlib.sha256(gh.tobytes()).hexdigest() == rec["heights_sha256"]
+    ctx = Context(0)
+    try:
+        wm, wh = ctx.cluster(keep, w.n, 1)
+    finally:
+        ctx.close()
+    assert np.array_equal(gm, wm.cpu().numpy())
+    assert np.array_equal(gh.view(np.uint32), wh.cpu().numpy().view(np.uint32))
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit():
     n = native.LW_NOALLOC_MAX_N + 1
     dD = torch.zeros(8, dtype=torch.float32, device="cuda")
