@@ -375,9 +375,24 @@ __device__ void exchange_requests(int cnt, const int (&rq)[kReqPerCta], int b, S
 }
 
 // KK smallest keys over every thread's sorted list; result in sh.tko (all threads).
-template <int NT, int S, int KK>
+// Barrier of the threads that work together: the whole CTA (TB == NT), or
+// its last TB threads (named barrier 1) while warp 0 does something else.
+template <int NT, int TB>
+__device__ __forceinline__ void team_sync()
+{
+    static_assert(TB % 32 == 0 && TB <= NT, "a team is whole warps");
+    if constexpr (TB == NT)
+        __syncthreads();
+    else
+        asm volatile("bar.sync 1, %0;" ::"n"(TB) : "memory");
+}
+
+// KK smallest keys over every thread's sorted list, for a team of the CTA's
+// last TB threads (default: all of them); result in sh.tko (team threads).
+template <int NT, int S, int KK, int TB = NT>
 __device__ void block_topk(u64 (&L)[KK], Shared<NT, S> &sh)
 {
+    constexpr int W0 = (NT - TB) / 32;  // first warp of the team
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u64 w[KK];
     warp_topk(L, w);
@@ -386,12 +401,12 @@ __device__ void block_topk(u64 (&L)[KK], Shared<NT, S> &sh)
         for (int q = 0; q < KK; ++q)
             sh.tk[warp][q] = w[q];
     }
-    __syncthreads();
-    if (warp == 0) {
+    team_sync<NT, TB>();
+    if (warp == W0) {
         u64 M[KK];
 #pragma unroll
         for (int q = 0; q < KK; ++q)
-            M[q] = lane < (NT / 32) ? sh.tk[lane][q] : kNoKey;
+            M[q] = lane < TB / 32 ? sh.tk[W0 + lane][q] : kNoKey;
         warp_topk(M, w);
         if (lane == 0) {
 #pragma unroll
@@ -399,7 +414,7 @@ __device__ void block_topk(u64 (&L)[KK], Shared<NT, S> &sh)
                 sh.tko[q] = w[q];
         }
     }
-    __syncthreads();
+    team_sync<NT, TB>();
 }
 
 // Grid-wide barrier, split in two so that a CTA can do work that nobody
@@ -530,11 +545,11 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
 // `live_cells`.  Result in sh.tko.
 // (Row scans are kept out of line: inside the round loop's register
 // allocation their loads in flight would be spilled.)
-template <int NT, int S>
+template <int NT, int S, int TB = NT>
 __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, const unsigned *bitmap,
-                                            Shared<NT, S> &sh,
-                               long long &live_cells)
+                                            Shared<NT, S> &sh, long long &live_cells)
 {
+    const int ts = threadIdx.x - (NT - TB);  // thread of the team
     const long long n = p.n;
     const long long start = row_base(p, r) + r + 1;
     const long long end = start + (n - r - 1);
@@ -560,23 +575,23 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
     if (a0 > end)
         a0 = end;
     const long long a1 = a0 + ((end - a0) & ~3LL);
-    for (long long q = start + threadIdx.x; q < a0; q += NT)
+    for (long long q = start + ts; q < a0; q += TB)
         take(__ldcg(p.D + q), q);
-    for (long long q = a1 + threadIdx.x; q < end; q += NT)
+    for (long long q = a1 + ts; q < end; q += TB)
         take(__ldcg(p.D + q), q);
     const float4 *D4 = reinterpret_cast<const float4 *>(p.D);
     const long long j1 = a1 >> 2;
-    for (long long j0 = (a0 >> 2) + threadIdx.x; j0 < j1; j0 += 8 * NT) {
+    for (long long j0 = (a0 >> 2) + ts; j0 < j1; j0 += 8 * TB) {
         float4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const long long j = j0 + (long long)u * NT;
+            const long long j = j0 + (long long)u * TB;
             v[u] = j < j1 ? __ldcg(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             if (v[u].x >= 0.0f) {
-                const long long q = (j0 + (long long)u * NT) << 2;
+                const long long q = (j0 + (long long)u * TB) << 2;
                 take(v[u].x, q);
                 take(v[u].y, q + 1);
                 take(v[u].z, q + 2);
@@ -585,7 +600,7 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
         }
     }
     live_cells += cnt;
-    block_topk(L, sh);
+    block_topk<NT, S, K, TB>(L, sh);
 }
 
 // block_row_topk in the row-log layout.  Row r's current cells are (a) r's
@@ -596,14 +611,15 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
 // Merges t0 .. t0 + L0 - 1 (the current round, L0 > 0 only after this CTA's
 // own pass 2) take their survivors from the round's chain in shared memory,
 // older ones from the merge list.  Result in sh.tko.
-template <int NT, int S>
+template <int NT, int S, int TB = NT>
 __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long r, const unsigned *bitmap,
                                    const unsigned *vpos, unsigned *newer, Shared<NT, S> &sh, long long t0,
                                    int L0, long long &live_cells, u64 *tlog = nullptr)
 {
-    // with phase timing on, thread 0 adds the time of the log part to
-    // tlog[0] and of the matrix part (and the top-K) to tlog[1]
-    u64 tm0 = tlog && threadIdx.x == 0 ? global_ns() : 0;
+    const int ts = threadIdx.x - (NT - TB);  // thread of the team
+    // with phase timing on, the team's first thread adds the time of the log
+    // part to tlog[0] and of the matrix part (and the top-K) to tlog[1]
+    u64 tm0 = tlog && ts == 0 ? global_ns() : 0;
     const long long n = p.n;
     const long long nwords = (n + 31) / 32;
     const int sr = __ldcg(p.stamp + r);
@@ -618,20 +634,20 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
         if (key < L[K - 1])  // the whole key: ties on the value stop here
             list_insert(L, key);
     };
-    for (long long w = threadIdx.x; w < nwords; w += NT)
+    for (long long w = ts; w < nwords; w += TB)
         newer[w] = 0u;
-    __syncthreads();
+    team_sync<NT, TB>();
     // (a) the log: latest merges after r's stamp, eight positions in flight
     const float *log = p.TL + r * p.pitch;
     const long long t1 = t0 + L0;
     {
         constexpr int U = 8;
-        for (long long q0 = (long long)sr + 1 + threadIdx.x; q0 < t1; q0 += U * NT) {
+        for (long long q0 = (long long)sr + 1 + ts; q0 < t1; q0 += U * TB) {
             float v[U];
             int c[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const long long q = q0 + (long long)u * NT;
+                const long long q = q0 + (long long)u * TB;
                 c[u] = -1;
                 if (q < t1 && ((vpos[q >> 5] >> (q & 31)) & 1u)) {
                     c[u] = q < t0 ? __ldcg(p.merges + 2 * q) : sh.pi[q - t0];
@@ -648,8 +664,8 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
             }
         }
     }
-    __syncthreads();
-    if (tlog && threadIdx.x == 0) {
+    team_sync<NT, TB>();
+    if (tlog && ts == 0) {
         const u64 now = global_ns();
         tlog[0] += now - tm0;
         tm0 = now;
@@ -662,26 +678,26 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
     if (c_a > n)
         c_a = n;
     const long long c_b = c_a + ((n - c_a) & ~3LL);
-    for (long long c = r + 1 + threadIdx.x; c < c_a; c += NT)
+    for (long long c = r + 1 + ts; c < c_a; c += TB)
         if (cur(c))
             take(__ldcg(row + c), c);
-    for (long long c = c_b + threadIdx.x; c < n; c += NT)
+    for (long long c = c_b + ts; c < n; c += TB)
         if (cur(c))
             take(__ldcg(row + c), c);
     {
         constexpr int U = 8;
         const float4 *R4 = reinterpret_cast<const float4 *>(row);
         const long long j1 = c_b >> 2;
-        for (long long j0 = (c_a >> 2) + threadIdx.x; j0 < j1; j0 += U * NT) {
+        for (long long j0 = (c_a >> 2) + ts; j0 < j1; j0 += U * TB) {
             float4 v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const long long j = j0 + (long long)u * NT;
+                const long long j = j0 + (long long)u * TB;
                 v[u] = j < j1 ? __ldcg(R4 + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const long long j = j0 + (long long)u * NT;
+                const long long j = j0 + (long long)u * TB;
                 if (j < j1) {
                     const long long c = j << 2;
                     const unsigned m4 = ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 15u;
@@ -698,8 +714,8 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
         }
     }
     live_cells += cnt;
-    block_topk(L, sh);
-    if (tlog && threadIdx.x == 0)
+    block_topk<NT, S, K, TB>(L, sh);
+    if (tlog && ts == 0)
         tlog[1] += global_ns() - tm0;
 }
 
@@ -1210,6 +1226,30 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
             if (tid == 32)
                 st_installs += ninst;
+            // ---- the refills asked for in the previous round, served now by
+            // warps 1.. while warp 0 walks (row s of the list by CTA s mod G):
+            // the K smallest keys of the row over live columns, as the
+            // previous round left it; the owner installs the list at the start
+            // of the next round and replays this round's merges on it
+            constexpr int TB = NT - 32;
+            const int nexec = sh.nexec;
+            for (int s2 = b; s2 < nexec; s2 += G) {
+                const long long rr = sh.exec_row[s2];
+                if (rr < 0 || rr >= n - 1)
+                    continue;  // the same for every thread of the team
+                if (p.full)
+                    block_row_topk_log<NT, S, TB>(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells,
+                                                  p.timing ? xscan : nullptr);
+                else
+                    block_row_topk<NT, S, TB>(p, rr, bitmap, sh, st_fill_cells);
+                if (tid - 32 < K / 2) {
+                    const int h = tid - 32;
+                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.parts + ((size_t)par * kMaxReq + s2) * K);
+                    __stcg(dst + h, make_ulonglong2(sh.tko[2 * h], sh.tko[2 * h + 1]));
+                }
+            }
+            if (tid == 32)
+                st_fills += nexec;
         }
         __syncthreads();
         lap(xs1);
@@ -1500,24 +1540,6 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (a < c)
                 sh.C[a][c] = lw_cell(p.linkage, sh.X[a][c], sh.Y[a][c], sh.ph[c], sh.szi[c], sh.szj[c],
                                      sh.szi[a] + sh.szj[a]);
-        }
-        {
-            const int nexec = sh.nexec;
-            for (int s2 = b; s2 < nexec; s2 += G) {
-                const long long rr = sh.exec_row[s2];
-                if (rr < 0 || rr >= n - 1)
-                    continue;  // the same for every thread of the CTA
-                if (p.full)
-                    block_row_topk_log(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells,
-                                       p.timing ? xscan : nullptr);
-                else
-                    block_row_topk(p, rr, bitmap, sh, st_fill_cells);
-                if (tid < K / 2) {
-                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.parts + ((size_t)par * kMaxReq + s2) * K);
-                    __stcg(dst + tid, make_ulonglong2(sh.tko[2 * tid], sh.tko[2 * tid + 1]));
-                }
-            }
-            st_fills += nexec;
         }
         lap(ph3);
         if (!grid_wait(p, epoch, sh))
@@ -1954,8 +1976,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         atomicAdd(St + 2, (u64)st_updates);
         atomicAdd(St + 5, (u64)st_fill_cells);
         atomicAdd(St + 15, (u64)st_resc_cells);
-        if (tid == 32)
+        if (tid == 32) {
             atomicAdd(St + 6, (u64)st_installs);
+            if (b == 0)
+                St[4] = (u64)st_fills;  // every CTA read the same request lists
+            if (p.timing) {
+                atomicAdd(St + 24, xscan[0]);
+                atomicAdd(St + 25, xscan[1]);
+            }
+        }
         if (tid == 0)
             atomicAdd(St + 14, (u64)st_rescans);
         if (tid == 0) {
@@ -1964,7 +1993,6 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 St[1] = (u64)st_idle;
                 St[7] = (u64)st_walk;
                 St[3] = (u64)G;
-                St[4] = (u64)st_fills;
             }
             if (p.timing) {
                 ph1 += xs0 + xs1 + xs2;
@@ -1976,9 +2004,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 atomicAdd(St + 11, ph3);
                 atomicAdd(St + 12, ph4);
                 atomicAdd(St + 13, ph5);
-                const u64 xs[11] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7, xscan[0], xscan[1], xwalk};
-                for (int q = 0; q < 11; ++q)
+                const u64 xs[8] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7};
+                for (int q = 0; q < 8; ++q)
                     atomicAdd(St + 16 + q, xs[q]);
+                atomicAdd(St + 26, xwalk);
             }
         }
     }
