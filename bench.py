@@ -745,7 +745,7 @@ def run_serving(args, local):
     del bank
     plain_jobs_per_s = count / (plain_ms * 1e-3)
     best = max(results, key=lambda r: r["jobs_per_s"] or 0)
-    sustained = [r for r in results if r["jobs_per_s"] and r["jobs_per_s"] >= 0.95 * r["offered_rate"]]
+    sustained = [r for r in results if r["jobs_per_s"] and r["jobs_per_s"] >= 0.9 * r["offered_rate"]]
     return {
         "metric": "served jobs/s and latency (Poisson arrivals, n log-uniform [256, 32768], mixed linkage)",
         "value": best["jobs_per_s"], "unit": "jobs/s", "rates": results,

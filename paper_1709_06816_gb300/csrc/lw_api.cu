@@ -273,6 +273,17 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     return LW_OK;
 }
 
+}  // namespace
+
+int lw::reserve_workspace(lw_ctx *ctx, long long n)
+{
+    if (!ctx || n < 2)
+        return LW_ERR_INVALID_ARG;
+    return ensure(ctx, &ctx->ws, &ctx->ws_cap, lw::workspace_layout(n, ctx->num_sms).total, "workspace");
+}
+
+namespace {
+
 // Copy status/stats back and wait; maps the kernel status word.
 lw_status finish(lw_ctx *ctx)
 {

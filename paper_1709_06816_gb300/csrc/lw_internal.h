@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct lw_ctx;
+
 namespace lw {
 
 constexpr int kThreads = 512;            // default threads per CTA of the merge kernel
@@ -149,6 +151,12 @@ size_t merge_smem_bytes(long long n, int G, int nt);
 // True if a grid of G CTAs of nt threads for n objects fits co-resident on
 // the current device.
 bool merge_config_ok(long long n, int G, int num_sms, int nt = kThreads);
+// Size the context's device workspace for every run of up to n objects, so
+// that later runs never allocate (the serving loop reserves its lanes' at
+// creation: growing a workspace frees the old one, and cudaFree waits for
+// the whole device).  Returns LW_OK or LW_ERR_OOM.
+int reserve_workspace(struct ::lw_ctx *ctx, long long n);
+
 // Launch the persistent kernel (CTAs of nt threads) cooperatively on `stream`.
 cudaError_t launch_merge(const MergeParams &p, int nt, cudaStream_t stream);
 // CTAs of nt threads of the batch kernel that fit on one SM for jobs up to n_max.

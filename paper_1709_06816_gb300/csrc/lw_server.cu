@@ -24,8 +24,10 @@
 // (cooperative launches on different lanes run concurrently).
 
 #include "../../include/lw.h"
+#include "lw_internal.h"
 
 #include <cuda_runtime.h>
+#include <cmath>
 
 #include <algorithm>
 #include <atomic>
@@ -90,6 +92,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct lw_server {
     int device = 0;
     int num_sms = 0;
+    long long n_max = 2;  // largest n whose packed triangle fits the pool
     char *pool = nullptr;
     size_t budget = 0;
     std::map<size_t, size_t> free_blocks;  // offset -> size
@@ -177,17 +180,20 @@ struct lw_server {
         float *dh = r.heights;
         if (!dev_out) {
             if (L.out_cap < (size_t)(r.n - 1)) {
+                // once per lane, for the largest request the pool can hold:
+                // cudaFree of a smaller buffer would wait for the whole device
                 cudaFree(L.dm);
                 cudaFree(L.dh);
                 L.dm = nullptr;
                 L.dh = nullptr;
                 L.out_cap = 0;
-                if (cudaMalloc(&L.dm, sizeof(int32_t) * 2 * (size_t)(r.n - 1)) != cudaSuccess ||
-                    cudaMalloc(&L.dh, sizeof(float) * (size_t)(r.n - 1)) != cudaSuccess) {
+                const size_t steps = (size_t)(n_max > r.n ? n_max : r.n) - 1;
+                if (cudaMalloc(&L.dm, sizeof(int32_t) * 2 * steps) != cudaSuccess ||
+                    cudaMalloc(&L.dh, sizeof(float) * steps) != cudaSuccess) {
                     cudaGetLastError();
                     return LW_ERR_OOM;
                 }
-                L.out_cap = (size_t)(r.n - 1);
+                L.out_cap = steps;
             }
             dm = L.dm;
             dh = L.dh;
@@ -329,6 +335,12 @@ lw_status lw_server_create(int device, int64_t budget_bytes, int32_t lanes, lw_s
         return LW_ERR_OOM;
     }
     s->free_blocks[0] = s->budget;
+    long long n_max = (long long)std::sqrt(2.0 * (double)(s->budget / sizeof(float))) + 2;
+    while (n_max > 2 && up256((size_t)n_max * (size_t)(n_max - 1) / 2 * sizeof(float)) > s->budget)
+        --n_max;
+    if (n_max > LW_MAX_N)
+        n_max = LW_MAX_N;
+    s->n_max = n_max;
     s->lanes.resize((size_t)lanes);
     for (Lane &L : s->lanes) {
         lw_status st = LW_OK;
@@ -337,6 +349,11 @@ lw_status lw_server_create(int device, int64_t budget_bytes, int32_t lanes, lw_s
             st = LW_ERR_CUDA;
         if (st == LW_OK)
             st = lw_create(&L.ctx, device, L.stream);
+        // the workspace for the largest request the pool can hold, now: a
+        // lane that grew it later would free the old one, and cudaFree
+        // waits for the whole device (every other lane's work)
+        if (st == LW_OK)
+            st = (lw_status)lw::reserve_workspace(L.ctx, n_max);
         if (st != LW_OK) {
             cudaGetLastError();
             lw_server_destroy(s);
