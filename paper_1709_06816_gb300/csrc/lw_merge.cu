@@ -95,14 +95,14 @@ __device__ __forceinline__ long long row_base(const MergeParams &p, long long r)
 }
 
 
-// Cell {x, y} read directly (the cells between members of a round's chain).
-// Row-log layout: the cell is current in the row of M whose slot was stamped
-// later (both rows hold the input value while neither slot has merged).
-__device__ __forceinline__ float member_cell(const MergeParams &p, long long x, long long y)
+// Cell {x, y} read directly (the cells between members of a round's chain),
+// the slots' stamps sx, sy given.  Row-log layout: the cell is current in the
+// row of M whose slot was stamped later (both rows hold the input value
+// while neither slot has merged).
+__device__ __forceinline__ float member_cell(const MergeParams &p, long long x, int sx, long long y, int sy)
 {
     if (!p.full)
         return __ldcg(p.D + pair_idx(x, y, p.n));
-    const int sx = __ldcg(p.stamp + x), sy = __ldcg(p.stamp + y);
     return sx >= sy ? __ldcg(p.D + x * p.pitch + y) : __ldcg(p.D + y * p.pitch + x);
 }
 
@@ -671,7 +671,11 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
         tm0 = now;
     }
     // (b) row r of M at live columns c > r not found in the log: 16-byte
-    // pieces (rows start 16-byte aligned), eight in flight per thread
+    // pieces (rows start 16-byte aligned), eight in flight per thread.  The
+    // first batch also gives a bound: the 4th smallest of the team's
+    // per-thread minima is the key of a real cell with at least three real
+    // cells below it, so no cell above it can be among the row's four
+    // smallest; after it only cells at or below it reach the lists.
     const float *row = p.D + r * p.pitch;
     auto cur = [&](long long c) { return ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 1u; };
     long long c_a = (r + 4) & ~3LL;  // first multiple of 4 above r
@@ -688,12 +692,38 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
         constexpr int U = 8;
         const float4 *R4 = reinterpret_cast<const float4 *>(row);
         const long long j1 = c_b >> 2;
-        for (long long j0 = (c_a >> 2) + ts; j0 < j1; j0 += U * TB) {
+        u64 thr = kNoKey;
+        bool first = true;
+        for (long long j0 = (c_a >> 2) + ts;; j0 += U * TB) {
+            if (!first && j0 >= j1)
+                break;  // (every thread of the team runs the first batch: it holds a barrier)
             float4 v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const long long j = j0 + (long long)u * TB;
                 v[u] = j < j1 ? __ldcg(R4 + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            if (first) {
+                u64 mn = kNoKey;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long j = j0 + (long long)u * TB;
+                    if (j < j1) {
+                        const long long c = j << 2;
+                        const unsigned m4 = ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 15u;
+                        const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const u64 k = make_key(vv[e], (unsigned)(c + e));
+                            if (((m4 >> e) & 1u) && k < mn)
+                                mn = k;
+                        }
+                    }
+                }
+                u64 M4[K] = {mn, kNoKey, kNoKey, kNoKey};
+                block_topk<NT, S, K, TB>(M4, sh);
+                thr = sh.tko[K - 1];
+                first = false;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -701,14 +731,14 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
                 if (j < j1) {
                     const long long c = j << 2;
                     const unsigned m4 = ((bitmap[c >> 5] & ~newer[c >> 5]) >> (c & 31)) & 15u;
-                    if (m4 & 1u)
-                        take(v[u].x, c);
-                    if (m4 & 2u)
-                        take(v[u].y, c + 1);
-                    if (m4 & 4u)
-                        take(v[u].z, c + 2);
-                    if (m4 & 8u)
-                        take(v[u].w, c + 3);
+                    cnt += __popc(m4);
+                    const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const u64 k = make_key(vv[e], (unsigned)(c + e));
+                        if (((m4 >> e) & 1u) && k <= thr && k < L[K - 1])
+                            list_insert(L, k);
+                    }
                 }
             }
         }
@@ -1098,6 +1128,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             // member 2a = i_a, 2a + 1 = j_a: lane l holds members l and l + 32
             int member0 = -1, member1 = -1;
             unsigned front = 0;  // value bits of the last entry visited
+            // lane a loads the sizes and stamps of pair a as soon as it is
+            // proposed: they arrive while the walk goes on
+            int q_szi = 0, q_szj = 0, q_si = 0, q_sj = 0;
             for (int guard = 0; guard <= G * PUB; ++guard) {
                 const u64 m = warp_u64_min(lm);
                 if (m == kNoKey)
@@ -1143,6 +1176,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                                 sh.pj[np] = c;
                                 sh.ph[np] = __uint_as_float((unsigned)(m >> 32));
                             }
+                            // (a pair out of range is caught before any other access)
+                            if (lane == np && row >= 0 && row < c && c < n) {
+                                q_szi = __ldcg(p.size_g + row);
+                                q_szj = __ldcg(p.size_g + c);
+                                if (p.full) {
+                                    q_si = __ldcg(p.stamp + row);
+                                    q_sj = __ldcg(p.stamp + c);
+                                }
+                            }
                             ++np;
                             if (np == S)
                                 stop = true;
@@ -1155,6 +1197,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (lane == 0) {
                 sh.np = np;
                 sh.front = front;
+            }
+            __syncwarp();
+            if (lane < np) {
+                sh.szi[lane] = q_szi;
+                sh.szj[lane] = q_szj;
+                sh.si[lane] = q_si;
+                sh.sj[lane] = q_sj;
+                sh.bi[lane] = row_base(p, sh.pi[lane]);  // cell (i, c) at bi + c (packed: for c > i)
+                sh.bj[lane] = row_base(p, sh.pj[lane]);
             }
             if (p.timing && tid == 0)
                 xwalk += global_ns() - twalk0;
@@ -1274,15 +1325,6 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             sh.wam[e / S][e % S] = kNoKey;
             sh.whm[e / S][e % S] = kNoKey;
         }
-        if (tid < s) {
-            sh.szi[tid] = __ldcg(p.size_g + sh.pi[tid]);
-            sh.szj[tid] = __ldcg(p.size_g + sh.pj[tid]);
-            const long long i = sh.pi[tid], j = sh.pj[tid];
-            sh.bi[tid] = row_base(p, i);  // cell (i, c) at bi + c (packed: for c > i)
-            sh.bj[tid] = row_base(p, j);
-            sh.si[tid] = p.full ? __ldcg(p.stamp + i) : 0;
-            sh.sj[tid] = p.full ? __ldcg(p.stamp + j) : 0;
-        }
         if (tid < 2 * s) {
             const long long m = (tid & 1) ? sh.pj[tid >> 1] : sh.pi[tid >> 1];
             if (owner_of(m) == b)
@@ -1304,7 +1346,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (e < 4 * S * S && u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
                     const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                     const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                    dmv[q] = member_cell(p, mu, mv);
+                    const int su = (u & 1) ? sh.sj[u >> 1] : sh.si[u >> 1];
+                    const int sv = (v & 1) ? sh.sj[v >> 1] : sh.si[v >> 1];
+                    dmv[q] = member_cell(p, mu, su, mv, sv);
                 }
             }
         } else {
@@ -1313,7 +1357,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (u < v && v < 2 * s && (u >> 1) != (v >> 1)) {
                     const long long mu = (u & 1) ? sh.pj[u >> 1] : sh.pi[u >> 1];
                     const long long mv = (v & 1) ? sh.pj[v >> 1] : sh.pi[v >> 1];
-                    const float d = member_cell(p, mu, mv);
+                    const int su = (u & 1) ? sh.sj[u >> 1] : sh.si[u >> 1];
+                    const int sv = (v & 1) ? sh.sj[v >> 1] : sh.si[v >> 1];
+                    const float d = member_cell(p, mu, su, mv, sv);
                     sh.Dm[u][v] = d;
                     sh.Dm[v][u] = d;
                 }
