@@ -139,18 +139,27 @@ lw_status lw_wait(lw_ctx *ctx);
  *   [7] published entries the walks visited (all rounds),
  *   [8..13] with LW_OPT_PHASE_TIMES on: wall-clock nanoseconds summed over
  *       the CTAs of the grid, per phase of a round: [8] barrier waits,
- *       [9] exchange, walk and refill installs, [10] pass 1 (new cells, read
- *       only), [11] refill service in the barrier window, [12] certification
- *       and bookkeeping, [13] pass 2 (writes, cache upkeep) and publish;
+ *       [9] exchange, walk, refill installs and scans, [10] pass 1 (new cells, read
+ *       only), [11] the cells after two merges, computed in the window of
+ *       the second barrier, [12] certification and bookkeeping, [13] pass 2
+ *       (writes, cache upkeep) and publish;
  *   [14] rows rescanned at once by their owner (cache emptied),
  *   [15] live cells read by those rescans,
  *   [16..25] with LW_OPT_PHASE_TIMES on, a finer split of [9], [11], [12]
  *       and [13] (same units): [16] reading the CTAs' records, [17] the
- *       walk and refill installs, [18] the chain's sizes, stamps and member
+ *       walk with the refill installs and scans beside it, [18] the
+ *       chain's sizes, stamps and member
  *       cells, [19] the cross-CTA minima of the new cells, [20] the
  *       certification, [21] bookkeeping and survivor caches, [22] pass 2,
  *       [23] owner rescans; refill scans in the row-log layout: [24] the
- *       log part, [25] the matrix part; [26] the walk alone (part of [17]).
+ *       log part, [25] the matrix part; [26] the walk alone (part of [17]);
+ *   [27..32] with LW_OPT_PHASE_TIMES on, the barriers' own cost: [27] the
+ *       waits (ns) of the CTA that arrived last, summed over the barriers
+ *       of the loop, [28] those barriers (as counted by the CTAs that
+ *       completed them), [29] of them the second barrier of a round, [30]
+ *       second barriers completed by a CTA serving a refill that round,
+ *       [31] first barriers completed by such a CTA, [32] barriers
+ *       completed by CTA 0.
  */
 lw_status lw_get_stats(lw_ctx *ctx, int64_t *stats, int count);
 

@@ -20,7 +20,7 @@ constexpr int kRefillAt = 0;             // ask for a refill when the cache hold
 constexpr int kSurvivorRefillAt = 1;     // the same for a survivor row right after its merge
 constexpr int kMaxReq = 256;             // refill requests served per round
 constexpr int kReqPerCta = 8;            // refill requests one CTA may make per round
-constexpr int kStats = 27;
+constexpr int kStats = 33;
 constexpr uint64_t kNoKey = ~0ull;
 
 // Column word of a published entry: the column, or one of two stop marks.

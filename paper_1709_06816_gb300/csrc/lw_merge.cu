@@ -130,6 +130,28 @@ __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned atom_release_add(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// 16 bytes global -> shared, cached in L2 only (the words read are written by
+// other CTAs between grid barriers, so L1 must not hold them).  The copy
+// writes no register: a warp that issues one per step does not wait for the
+// previous one.
+__device__ __forceinline__ void copy16_async(void *dst_smem, const void *src_gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src_gmem) : "memory");
+}
+
+__device__ __forceinline__ void copy_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ u64 global_ns()
 {
     u64 t;
@@ -310,6 +332,8 @@ struct Shared {
     int szi[S], szj[S];
     long long bi[S], bj[S];      // row bases of the members: cell (x, c) at b + c
     int si[S], sj[S];            // row-log layout: the members' stamps before the round
+    // the 16-byte words holding size_g[i_a], size_g[j_a], stamp[i_a], stamp[j_a]
+    alignas(16) int qw[S][16];
     u64 wam[W][S], whm[W][S];    // per warp: smallest new cell per pair (all k, k > i)
     u64 gamin[S], ghmin[S];      // the same over all CTAs
     // (rows padded by one word: the certification reads a column of these
@@ -322,6 +346,13 @@ struct Shared {
     int ppi[S], ppj[S];
     int nprev;
     int nresc;                   // rows to rescan at once this round
+    // phase timers and the counters one thread keeps (thread 0, thread 32 for
+    // the refill team): here rather than in registers of the round loop
+    struct {
+        u64 ph[6], xs[8], xscan[2], xwalk, xlast, tmark;
+        long long fills, installs, rounds, idle, walk, rescans;
+        long long nlast, nlast_b, nlast_b_scan, nlast_a_scan;
+    } ty;
 };
 
 // After barrier A: the list of rows to refill in this round -- every CTA's
@@ -423,13 +454,19 @@ __device__ void block_topk(u64 (&L)[KK], Shared<NT, S> &sh)
 // are published).  wait: that thread spins with acquire loads until every
 // CTA has arrived, bounded by a wall-clock limit; returns false when the run
 // must stop (this CTA gave up, or another CTA flagged an error).
-__device__ __forceinline__ void grid_arrive(const MergeParams &p, unsigned &epoch)
+// With `last` given (phase timing), thread 0 also learns whether its CTA
+// was the last to arrive.
+__device__ __forceinline__ void grid_arrive(const MergeParams &p, unsigned &epoch, bool *last = nullptr)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1;
-        if (p.G > 1)
-            red_release_add(p.bar, 1u);
+        if (p.G > 1) {
+            if (last)
+                *last = atom_release_add(p.bar, 1u) + 1u == epoch * (unsigned)p.G;
+            else
+                red_release_add(p.bar, 1u);
+        }
     }
 }
 
@@ -749,6 +786,120 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
         tlog[1] += global_ns() - tm0;
 }
 
+// block_row_topk in the row-log layout, column by column: live column c > r
+// holds its current cell in row r of M when c's stamp is not after r's, and
+// otherwise in r's log at c's stamp (written by that merge).  The stamps are
+// read beside the row (16-byte pieces of both, two of each per thread and
+// batch), then the log cells of the columns stamped after r: two dependent
+// reads per batch and no pass over the merge list.  (A deeper batch holds
+// more registers across the call, and the caller, the round loop, then
+// spills: two pieces measured fastest.)  Needs p.D and p.stamp 16-byte
+// aligned (rows are, the pitch being a multiple of 4).  The first batch
+// gives a bound when the row has more than one batch (see
+// block_row_topk_log).  Result in sh.tko.
+template <int NT, int S, int TB = NT>
+__device__ __noinline__ void block_row_topk_cols(const MergeParams &p, long long r, const unsigned *bitmap,
+                                                 Shared<NT, S> &sh, long long &live_cells, u64 *tlog = nullptr)
+{
+    const int ts = threadIdx.x - (NT - TB);  // thread of the team
+    const u64 tm0 = tlog && ts == 0 ? global_ns() : 0;
+    const long long n = p.n;
+    const int sr = __ldcg(p.stamp + r);
+    const float *row = p.D + r * p.pitch;
+    const float *log = p.TL + r * p.pitch;
+    u64 L[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        L[q] = kNoKey;
+    long long cnt = 0;
+    auto one = [&](long long c) {
+        if (live(bitmap, c)) {
+            ++cnt;
+            const int sc = __ldcg(p.stamp + c);
+            const float v = sc > sr ? __ldcg(log + sc) : __ldcg(row + c);
+            const u64 key = make_key(v, (unsigned)c);
+            if (key < L[K - 1])
+                list_insert(L, key);
+        }
+    };
+    long long c_a = (r + 4) & ~3LL;  // first multiple of 4 above r
+    if (c_a > n)
+        c_a = n;
+    const long long c_b = c_a + ((n - c_a) & ~3LL);
+    for (long long c = r + 1 + ts; c < c_a; c += TB)
+        one(c);
+    for (long long c = c_b + ts; c < n; c += TB)
+        one(c);
+    {
+        constexpr int U = 2;
+        const float4 *R4 = reinterpret_cast<const float4 *>(row);
+        const int4 *S4 = reinterpret_cast<const int4 *>(p.stamp);
+        const long long j0a = c_a >> 2, j1 = c_b >> 2;
+        // a bound from the first batch only pays when more batches follow
+        bool first = j1 - j0a > (long long)U * TB;
+        u64 thr = kNoKey;
+        for (long long j0 = j0a + ts;; j0 += U * TB) {
+            if (!first && j0 >= j1)
+                break;  // (every thread of the team runs a first batch: it holds a barrier)
+            float v[U][4];
+            int sc[U][4];
+            unsigned m4[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long j = j0 + (long long)u * TB;
+                m4[u] = 0u;
+                if (j < j1) {
+                    const float4 a = __ldcg(R4 + j);
+                    const int4 b = __ldcg(S4 + j);
+                    v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+                    sc[u][0] = b.x; sc[u][1] = b.y; sc[u][2] = b.z; sc[u][3] = b.w;
+                    const long long c = j << 2;
+                    m4[u] = (bitmap[c >> 5] >> (c & 31)) & 15u;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (((m4[u] >> e) & 1u) && sc[u][e] > sr)
+                        v[u][e] = __ldcg(log + sc[u][e]);
+            }
+            if (first) {
+                u64 mn = kNoKey;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long c = (j0 + (long long)u * TB) << 2;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const u64 k = make_key(v[u][e], (unsigned)(c + e));
+                        if (((m4[u] >> e) & 1u) && k < mn)
+                            mn = k;
+                    }
+                }
+                u64 M4[K] = {mn, kNoKey, kNoKey, kNoKey};
+                block_topk<NT, S, K, TB>(M4, sh);
+                thr = sh.tko[K - 1];
+                first = false;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long c = (j0 + (long long)u * TB) << 2;
+                cnt += __popc(m4[u]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const u64 k = make_key(v[u][e], (unsigned)(c + e));
+                    if (((m4[u] >> e) & 1u) && k <= thr && k < L[K - 1])
+                        list_insert(L, k);
+                }
+            }
+        }
+    }
+    live_cells += cnt;
+    block_topk<NT, S, K, TB>(L, sh);
+    if (tlog && ts == 0)
+        tlog[1] += global_ns() - tm0;
+}
+
 // K smallest keys of row r over live columns, computed by one warp (the
 // rows of a one-CTA job are refreshed this way, several warps side by side).
 // Adds the live cells read to `live_cells`.  Result in out (all lanes).
@@ -889,25 +1040,37 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     };
 
     // per-phase wall-clock totals of this CTA (thread 0), when timing is on
-    u64 ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
+    auto &ty = sh.ty;
+    u64 &ph0 = ty.ph[0], &ph1 = ty.ph[1], &ph2 = ty.ph[2], &ph3 = ty.ph[3], &ph4 = ty.ph[4], &ph5 = ty.ph[5];
     // finer split: ph1 = xs0 (records) + xs1 (walk, installs) + xs2 (chain
     // sizes, stamps, member cells); ph4 = xs3 (cross-CTA minima) + xs4
     // (certification) + xs5 (bookkeeping, survivor caches); ph5 = xs6 (pass 2)
     // + xs7 (owner rescans) + the publish
-    u64 xs0 = 0, xs1 = 0, xs2 = 0, xs3 = 0, xs4 = 0, xs5 = 0, xs6 = 0, xs7 = 0;
-    u64 xscan[2] = {0, 0};  // refill scans in the row-log layout: log part, matrix part
-    u64 xwalk = 0;          // the walk itself (warp 0)
-    u64 tmark = 0;
+    u64 &xs0 = ty.xs[0], &xs1 = ty.xs[1], &xs2 = ty.xs[2], &xs3 = ty.xs[3];
+    u64 &xs4 = ty.xs[4], &xs5 = ty.xs[5], &xs6 = ty.xs[6], &xs7 = ty.xs[7];
+    // ty.xscan: refill scans in the row-log layout (log part, matrix part);
+    // ty.xwalk: the walk itself (warp 0); ty.xlast, ty.nlast: barriers this
+    // CTA completed (arrived last at), its wait then being the barrier's own
+    // latency, with counts of those at B (nlast_b) and of those while serving
+    // a refill scan (at B, at A)
+    if (tid == 0) {
+        for (int q = 0; q < 6; ++q)
+            ty.ph[q] = 0;
+        for (int q = 0; q < 8; ++q)
+            ty.xs[q] = 0;
+        ty.xscan[0] = ty.xscan[1] = ty.xwalk = ty.xlast = ty.tmark = 0;
+        ty.fills = ty.installs = ty.rounds = ty.idle = ty.walk = ty.rescans = 0;
+        ty.nlast = ty.nlast_b = ty.nlast_b_scan = ty.nlast_a_scan = 0;
+    }
     auto lap = [&](u64 &acc) {
         if (p.timing && threadIdx.x == 0) {
             const u64 now = global_ns();
-            acc += now - tmark;
-            tmark = now;
+            acc += now - ty.tmark;
+            ty.tmark = now;
         }
     };
 
-    long long st_updates = 0, st_fill_cells = 0, st_rescans = 0, st_resc_cells = 0;
-    long long st_fills = 0, st_installs = 0, st_rounds = 0, st_idle = 0, st_walk = 0;
+    long long st_updates = 0, st_fill_cells = 0, st_resc_cells = 0;
 
     // The records of round rr: this CTA's PUB smallest entries (cached keys
     // and bound marks of its rows) and its refill requests of round rr - 1.
@@ -1040,7 +1203,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
     if (sh.flag != 0)
         return;
     if (p.timing && tid == 0)
-        tmark = global_ns();
+        ty.tmark = global_ns();
 
     long long t = 0;   // merges done
     const long long max_rounds = 2 * n + 64;
@@ -1128,14 +1291,18 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             // member 2a = i_a, 2a + 1 = j_a: lane l holds members l and l + 32
             int member0 = -1, member1 = -1;
             unsigned front = 0;  // value bits of the last entry visited
-            // lane a loads the sizes and stamps of pair a as soon as it is
-            // proposed: they arrive while the walk goes on
+            // lane a fetches the sizes and stamps of pair a as soon as it is
+            // accepted: they arrive while the walk goes on (asynchronous copies
+            // of the aligned words around them, when the arrays allow it)
+            const bool qa = ((reinterpret_cast<uintptr_t>(p.size_g) |
+                              reinterpret_cast<uintptr_t>(p.stamp)) & 15u) == 0;
             int q_szi = 0, q_szj = 0, q_si = 0, q_sj = 0;
+            int nwalk = 0;
             for (int guard = 0; guard <= G * PUB; ++guard) {
                 const u64 m = warp_u64_min(lm);
                 if (m == kNoKey)
                     break;
-                ++st_walk;
+                ++nwalk;
                 front = (unsigned)(m >> 32);
                 const int src = __ffs(__ballot_sync(kFull, lm == m)) - 1;
                 unsigned col = 0;
@@ -1178,11 +1345,22 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                             }
                             // (a pair out of range is caught before any other access)
                             if (lane == np && row >= 0 && row < c && c < n) {
-                                q_szi = __ldcg(p.size_g + row);
-                                q_szj = __ldcg(p.size_g + c);
-                                if (p.full) {
-                                    q_si = __ldcg(p.stamp + row);
-                                    q_sj = __ldcg(p.stamp + c);
+                                if (qa) {
+                                    // (the arrays are padded to whole 16-byte words)
+                                    int *w = sh.qw[np];
+                                    copy16_async(w, p.size_g + (row & ~3));
+                                    copy16_async(w + 4, p.size_g + (c & ~3));
+                                    if (p.full) {
+                                        copy16_async(w + 8, p.stamp + (row & ~3));
+                                        copy16_async(w + 12, p.stamp + (c & ~3));
+                                    }
+                                } else {
+                                    q_szi = __ldcg(p.size_g + row);
+                                    q_szj = __ldcg(p.size_g + c);
+                                    if (p.full) {
+                                        q_si = __ldcg(p.stamp + row);
+                                        q_sj = __ldcg(p.stamp + c);
+                                    }
                                 }
                             }
                             ++np;
@@ -1197,9 +1375,22 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (lane == 0) {
                 sh.np = np;
                 sh.front = front;
+                ty.walk += nwalk;
             }
+            copy_async_wait_all();
             __syncwarp();
             if (lane < np) {
+                const int row = sh.pi[lane], c = sh.pj[lane];
+                if (qa && row >= 0 && row < c && c < n) {
+                    // lane a issued pair a's copies, so they are complete
+                    const int *w = sh.qw[lane];
+                    q_szi = w[row & 3];
+                    q_szj = w[4 + (c & 3)];
+                    if (p.full) {
+                        q_si = w[8 + (row & 3)];
+                        q_sj = w[12 + (c & 3)];
+                    }
+                }
                 sh.szi[lane] = q_szi;
                 sh.szj[lane] = q_szj;
                 sh.si[lane] = q_si;
@@ -1208,7 +1399,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 sh.bj[lane] = row_base(p, sh.pj[lane]);
             }
             if (p.timing && tid == 0)
-                xwalk += global_ns() - twalk0;
+                ty.xwalk += global_ns() - twalk0;
         } else {
             // ---- refills served in the previous round: take the row's list,
             // then replay that round's merges (the scan ran before them, or
@@ -1276,7 +1467,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
             }
             if (tid == 32)
-                st_installs += ninst;
+                ty.installs += ninst;
             // ---- the refills asked for in the previous round, served now by
             // warps 1.. while warp 0 walks (row s of the list by CTA s mod G):
             // the K smallest keys of the row over live columns, as the
@@ -1284,13 +1475,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             // of the next round and replays this round's merges on it
             constexpr int TB = NT - 32;
             const int nexec = sh.nexec;
+            const bool cols_ok = ((reinterpret_cast<uintptr_t>(p.D) | reinterpret_cast<uintptr_t>(p.stamp)) & 15u) == 0;
             for (int s2 = b; s2 < nexec; s2 += G) {
                 const long long rr = sh.exec_row[s2];
                 if (rr < 0 || rr >= n - 1)
                     continue;  // the same for every thread of the team
-                if (p.full)
+                if (p.full && cols_ok)
+                    block_row_topk_cols<NT, S, TB>(p, rr, bitmap, sh, st_fill_cells, p.timing ? ty.xscan : nullptr);
+                else if (p.full)
                     block_row_topk_log<NT, S, TB>(p, rr, bitmap, vpos, newer, sh, t, 0, st_fill_cells,
-                                                  p.timing ? xscan : nullptr);
+                                                  p.timing ? ty.xscan : nullptr);
                 else
                     block_row_topk<NT, S, TB>(p, rr, bitmap, sh, st_fill_cells);
                 if (tid - 32 < K / 2) {
@@ -1300,7 +1494,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 }
             }
             if (tid == 32)
-                st_fills += nexec;
+                ty.fills += nexec;
         }
         __syncthreads();
         lap(xs1);
@@ -1562,7 +1756,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             }
         }
         lap(ph2);
-        grid_arrive(p, epoch);
+        bool last_b = false;
+        grid_arrive(p, epoch, p.timing ? &last_b : nullptr);
 
         // ---- window of barrier B: serve the refills asked for in round r - 1,
         // one CTA per row (row s of the list by CTA s mod G, all its threads):
@@ -1588,8 +1783,15 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                                      sh.szi[a] + sh.szj[a]);
         }
         lap(ph3);
+        const u64 twb = p.timing && tid == 0 ? global_ns() : 0;
         if (!grid_wait(p, epoch, sh))
             return;
+        if (p.timing && tid == 0 && last_b) {
+            ty.xlast += global_ns() - twb;
+            ++ty.nlast;
+            ++ty.nlast_b;
+            ty.nlast_b_scan += b < sh.nexec;
+        }
         lap(ph0);
 
         // ---- B: the global per-pair minima, then the certified prefix
@@ -1968,7 +2170,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     cB[l] = c == K ? top[K - 1] : kNoKey;
                 }
             }
-            st_rescans += nresc;
+            if (tid == 0)
+                ty.rescans += nresc;
             if (nresc > 0)
                 __syncthreads();
         } else {
@@ -1986,7 +2189,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     cB[l] = c == K ? sh.tko[K - 1] : kNoKey;
                 }
             }
-            st_rescans += nresc;
+            if (tid == 0)
+                ty.rescans += nresc;
             if (nresc > 0)
                 __syncthreads();  // the rescanned caches (written by thread 0) before anyone reads them
         }
@@ -2003,17 +2207,24 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         if (tid == 0) {
             sh.nprev = L;
             sh.nresc = 0;
-            ++st_rounds;
-            st_idle += L == 0;
+            ++ty.rounds;
+            ty.idle += L == 0;
         }
         t += L;
         if (t >= n - 1)
             break;  // that was the last merge
         publish(r + 1);
         lap(ph5);
-        grid_arrive(p, epoch);
+        bool last_a = false;
+        grid_arrive(p, epoch, p.timing ? &last_a : nullptr);
+        const u64 twa = p.timing && tid == 0 ? global_ns() : 0;
         if (!grid_wait(p, epoch, sh))
             return;
+        if (p.timing && tid == 0 && last_a) {
+            ty.xlast += global_ns() - twa;
+            ++ty.nlast;
+            ty.nlast_a_scan += b < sh.nexec;
+        }
         lap(ph0);
     }
 
@@ -2023,37 +2234,38 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         atomicAdd(St + 5, (u64)st_fill_cells);
         atomicAdd(St + 15, (u64)st_resc_cells);
         if (tid == 32) {
-            atomicAdd(St + 6, (u64)st_installs);
+            atomicAdd(St + 6, (u64)ty.installs);
             if (b == 0)
-                St[4] = (u64)st_fills;  // every CTA read the same request lists
+                St[4] = (u64)ty.fills;  // every CTA read the same request lists
             if (p.timing) {
-                atomicAdd(St + 24, xscan[0]);
-                atomicAdd(St + 25, xscan[1]);
+                atomicAdd(St + 24, ty.xscan[0]);
+                atomicAdd(St + 25, ty.xscan[1]);
             }
         }
-        if (tid == 0)
-            atomicAdd(St + 14, (u64)st_rescans);
         if (tid == 0) {
+            atomicAdd(St + 14, (u64)ty.rescans);
             if (b == 0) {
-                St[0] = (u64)st_rounds;
-                St[1] = (u64)st_idle;
-                St[7] = (u64)st_walk;
+                St[0] = (u64)ty.rounds;
+                St[1] = (u64)ty.idle;
+                St[7] = (u64)ty.walk;
                 St[3] = (u64)G;
             }
             if (p.timing) {
                 ph1 += xs0 + xs1 + xs2;
                 ph4 += xs3 + xs4 + xs5;
                 ph5 += xs6 + xs7;
-                atomicAdd(St + 8, ph0);
-                atomicAdd(St + 9, ph1);
-                atomicAdd(St + 10, ph2);
-                atomicAdd(St + 11, ph3);
-                atomicAdd(St + 12, ph4);
-                atomicAdd(St + 13, ph5);
-                const u64 xs[8] = {xs0, xs1, xs2, xs3, xs4, xs5, xs6, xs7};
+                for (int q = 0; q < 6; ++q)
+                    atomicAdd(St + 8 + q, ty.ph[q]);
                 for (int q = 0; q < 8; ++q)
-                    atomicAdd(St + 16 + q, xs[q]);
-                atomicAdd(St + 26, xwalk);
+                    atomicAdd(St + 16 + q, ty.xs[q]);
+                atomicAdd(St + 26, ty.xwalk);
+                atomicAdd(St + 27, ty.xlast);
+                atomicAdd(St + 28, (u64)ty.nlast);
+                atomicAdd(St + 29, (u64)ty.nlast_b);
+                atomicAdd(St + 30, (u64)ty.nlast_b_scan);
+                atomicAdd(St + 31, (u64)ty.nlast_a_scan);
+                if (b == 0)
+                    St[32] = (u64)ty.nlast;
             }
         }
     }

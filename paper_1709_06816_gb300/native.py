@@ -181,8 +181,8 @@ def lw_wait(ctx: int) -> None:
 
 def lw_get_stats(ctx: int) -> dict:
     lib = load()
-    a = (ctypes.c_int64 * 27)()
-    s = lib.lw_get_stats(ctx, a, 27)
+    a = (ctypes.c_int64 * 33)()
+    s = lib.lw_get_stats(ctx, a, 33)
     if s != 0:
         raise LwError(s, "lw_get_stats")
     out = {"rounds": a[0], "idle_rounds": a[1], "updated": a[2], "grid": a[3],
@@ -195,6 +195,14 @@ def lw_get_stats(ctx: int) -> dict:
         sub = ("records", "walk_installs", "chain", "minima", "certify", "bookkeeping", "pass2",
                "rescans", "scan_log", "scan_matrix", "walk_only")
         out["subphase_ms"] = {nm: a[16 + q] / G / 1e6 for q, nm in enumerate(sub)}
+        if a[28] > 0:
+            out["barrier_detail"] = {
+                "barriers": a[28],
+                "last_arriver_wait_us": a[27] / a[28] / 1e3,
+                "b_last_serving_refill": a[30] / max(1, a[29]),
+                "a_last_serving_refill": a[31] / max(1, a[28] - a[29]),
+                "last_is_cta0": a[32] / a[28],
+            }
     return out
 
 
