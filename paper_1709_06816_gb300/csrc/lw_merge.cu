@@ -1469,14 +1469,16 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             if (tid == 32)
                 ty.installs += ninst;
             // ---- the refills asked for in the previous round, served now by
-            // warps 1.. while warp 0 walks (row s of the list by CTA s mod G):
+            // warps 1.. while warp 0 walks (row s of the list by CTA
+            // G - 1 - s mod G: rows are owned in blocks of 32 from CTA 0 up,
+            // so the last CTAs own a block fewer and take the scans first):
             // the K smallest keys of the row over live columns, as the
             // previous round left it; the owner installs the list at the start
             // of the next round and replays this round's merges on it
             constexpr int TB = NT - 32;
             const int nexec = sh.nexec;
             const bool cols_ok = ((reinterpret_cast<uintptr_t>(p.D) | reinterpret_cast<uintptr_t>(p.stamp)) & 15u) == 0;
-            for (int s2 = b; s2 < nexec; s2 += G) {
+            for (int s2 = G - 1 - b; s2 < nexec; s2 += G) {
                 const long long rr = sh.exec_row[s2];
                 if (rr < 0 || rr >= n - 1)
                     continue;  // the same for every thread of the team
@@ -1759,13 +1761,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         bool last_b = false;
         grid_arrive(p, epoch, p.timing ? &last_b : nullptr);
 
-        // ---- window of barrier B: serve the refills asked for in round r - 1,
-        // one CTA per row (row s of the list by CTA s mod G, all its threads):
-        // the K smallest keys of the row over live columns.  Nobody rewrites a
-        // cell before the barrier except the cells of this round's merges,
-        // which the install replays.
-        // cells (i_a, i_b) and (i_a, j_b) after merge a alone, then (i_a, i_b)
-        // after merges a and b: read only after barrier B
+        // ---- window of barrier B: the cells (i_a, i_b) and (i_a, j_b) after
+        // merge a alone, then (i_a, i_b) after merges a and b (read only after
+        // barrier B)
         for (int e = tid; e < s * s; e += NT) {
             const int a = e / s, c = e % s;
             if (a != c) {
@@ -1790,7 +1788,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             ty.xlast += global_ns() - twb;
             ++ty.nlast;
             ++ty.nlast_b;
-            ty.nlast_b_scan += b < sh.nexec;
+            ty.nlast_b_scan += G - 1 - b < sh.nexec;
         }
         lap(ph0);
 
@@ -2223,7 +2221,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         if (p.timing && tid == 0 && last_a) {
             ty.xlast += global_ns() - twa;
             ++ty.nlast;
-            ty.nlast_a_scan += b < sh.nexec;
+            ty.nlast_a_scan += G - 1 - b < sh.nexec;
         }
         lap(ph0);
     }
