@@ -95,9 +95,13 @@ lw_status lw_create(lw_ctx **out, int device, void *cuda_stream);
  *                matrix and OVERWRITTEN in place (the paper's update rewrites
  *                row and column i in place, Section 5.3 step 6): keep a copy
  *                if needed.
- *                If it is a HOST pointer the library copies it to a device
- *                buffer owned by the context and leaves the host array
- *                unchanged (pinned memory gives the fastest copy).
+ *                If it is a HOST pointer the host array is left unchanged:
+ *                page-locked (pinned, mapped) memory is read in place by the
+ *                GPU, in one pass over the host link, when the run uses the
+ *                row-log layout (multi-CTA runs with room for it, see
+ *                LW_OPT_LAYOUT); otherwise, and for pageable memory, the
+ *                library copies it to a device buffer owned by the context.
+ *                Either way all n(n-1)/2 cells must be readable.
  *   n            number of objects, 1 <= n <= LW_MAX_N.  n == 1: no merges.
  *   linkage      an lw_linkage value.
  *   merges_out   int32[2*(n-1)], host or device: step t is

@@ -87,6 +87,18 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked, mapped host memory (the GPU reads it over
+// the host link), else null.
+const float *mapped_host_alias(const float *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<const float *>(a.devicePointer) : nullptr;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Failure-injection hook (LW_OPT_TEST_FAIL_ALLOC): consumes one injected
@@ -200,9 +212,13 @@ int choose_grid(lw_ctx *ctx, long long n)
     return lw::merge_config_ok(n, G, ctx->num_sms, nt) ? G : 0;
 }
 
-// Queue one run on ctx->stream.  dist/merges/heights are device pointers.
+// Queue one run on ctx->stream.  dist/merges/heights are device pointers;
+// with host_src, ddist is the device address of the caller's mapped host
+// matrix, which only the layout kernel reads: when the run would not use the
+// row-log layout (so the kernel would work in ddist itself), nothing is
+// queued and *declined is set.
 lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *dmerges,
-                  float *dheights)
+                  float *dheights, bool host_src = false, bool *declined = nullptr)
 {
     const int G = choose_grid(ctx, n);
     if (G <= 0) {
@@ -239,6 +255,10 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
             if (s != LW_OK)
                 return s;
         }
+    }
+    if (host_src && !use_full) {
+        *declined = true;
+        return LW_OK;
     }
 
     lw::MergeParams p;
@@ -405,15 +425,6 @@ lw_status lw_cluster(lw_ctx *ctx, float *dist, int64_t n, int linkage, int32_t *
         return cuda_fail(ctx, e, "cudaSetDevice");
 
     const size_t cells = (size_t)n * (size_t)(n - 1) / 2;
-    float *ddist = dist;
-    if (!is_device_ptr(dist)) {
-        s = ensure(ctx, (void **)&ctx->dbuf, &ctx->dbuf_cap, cells * sizeof(float), "matrix copy");
-        if (s != LW_OK)
-            return s;
-        if ((e = upload(ctx, ctx->dbuf, dist, cells * sizeof(float))) != cudaSuccess)
-            return cuda_fail(ctx, e, "matrix upload");
-        ddist = ctx->dbuf;
-    }
     const bool dev_m = is_device_ptr(merges_out), dev_h = is_device_ptr(heights_out);
     int32_t *dm = merges_out;
     float *dh = heights_out;
@@ -428,7 +439,29 @@ lw_status lw_cluster(lw_ctx *ctx, float *dist, int64_t n, int linkage, int32_t *
         if (!dev_h)
             dh = reinterpret_cast<float *>(static_cast<char *>(ctx->obuf) + align256(mbytes));
     }
-    s = enqueue(ctx, ddist, n, linkage, dm, dh);
+    if (is_device_ptr(dist)) {
+        s = enqueue(ctx, dist, n, linkage, dm, dh);
+    } else {
+        // A page-locked, mapped host matrix is read in place by the layout
+        // kernel (one pass over the host link, no staging copy) when the run
+        // uses the row-log layout; otherwise it is copied to the device.
+        bool declined = true;
+        const float *alias = mapped_host_alias(dist);
+        if (alias) {
+            declined = false;
+            s = enqueue(ctx, const_cast<float *>(alias), n, linkage, dm, dh, true, &declined);
+            if (s != LW_OK)
+                return s;
+        }
+        if (declined) {
+            s = ensure(ctx, (void **)&ctx->dbuf, &ctx->dbuf_cap, cells * sizeof(float), "matrix copy");
+            if (s != LW_OK)
+                return s;
+            if ((e = upload(ctx, ctx->dbuf, dist, cells * sizeof(float))) != cudaSuccess)
+                return cuda_fail(ctx, e, "matrix upload");
+            s = enqueue(ctx, ctx->dbuf, n, linkage, dm, dh);
+        }
+    }
     if (s != LW_OK)
         return s;
     if (!dev_m && (e = cudaMemcpyAsync(merges_out, dm, mbytes, cudaMemcpyDeviceToHost,

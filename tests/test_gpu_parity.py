@@ -212,7 +212,7 @@ def test_allocation_failure_is_reported_and_the_context_recovers():
 
 
 def test_host_buffers(ctx):
-    """Host matrix and host outputs: copied by the library, host input untouched."""
+    """Host matrix and host outputs, host input untouched."""
     n = 700
     D = synth.small_gmm(n, 9)
     keep = D.copy()
@@ -221,10 +221,32 @@ def test_host_buffers(ctx):
     assert isinstance(m, np.ndarray)
     assert np.array_equal(D, keep)
     _assert_same((m, h), oracle.cached(D, n, 2), "host buffers")
-    # pinned host input
+    # pinned host input: read in place by the layout kernel (row-log layout,
+    # several CTAs) or copied to the device (packed layout, or one CTA)
     P = torch.from_numpy(D).pin_memory()
-    m2, h2 = ctx.cluster(P, n, 2)
-    _assert_same((m2.numpy(), h2.numpy()), oracle.cached(D, n, 2), "pinned")
+    try:
+        for layout, grid in ((0, 0), (1, 7), (2, 7), (0, 1)):
+            ctx.set_layout(layout)
+            ctx.set_grid(grid)
+            m2, h2 = ctx.cluster(P, n, 2)
+            _assert_same((m2.numpy(), h2.numpy()), oracle.cached(D, n, 2), f"pinned layout={layout} grid={grid}")
+            assert np.array_equal(P.numpy(), keep)
+        # a bad cell in a pinned host matrix read in place is reported, -0 reads as +0
+        ctx.set_layout(1)
+        ctx.set_grid(7)
+        B = P.clone().pin_memory()
+        B[n + 3] = float("nan")
+        with pytest.raises(LwError) as e:
+            ctx.cluster(B, n, 2)
+        assert e.value.status == 2
+        Z = torch.from_numpy(synth.tie_heavy(n, 21)).pin_memory()
+        want = oracle.cached(Z.numpy().copy(), n, 0)
+        Z[Z == 0] = -0.0
+        m3, h3 = ctx.cluster(Z, n, 0)
+        _assert_same((m3.numpy(), h3.numpy()), want, "pinned -0")
+    finally:
+        ctx.set_layout(0)
+        ctx.set_grid(0)
 
 
 def test_invalid_inputs(ctx):
