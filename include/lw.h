@@ -64,7 +64,11 @@ typedef enum {
     LW_ERR_INVALID_ARG = 1,   /* bad n, linkage, pointer or handle */
     LW_ERR_INVALID_INPUT = 2, /* a NaN, infinite or negative distance */
     LW_ERR_OOM = 3,           /* device or host allocation failed */
-    LW_ERR_CUDA = 4,          /* a CUDA runtime call failed (see lw_last_error) */
+    LW_ERR_CUDA = 4,          /* a CUDA runtime call failed, or the kernel stopped on an
+                                 internal check (see lw_last_error); the bounds-checked
+                                 build of the library (liblw_checked.so, -DLW_CHECKED,
+                                 for testing) reports here a merge-kernel access outside
+                                 the job's buffers, with its source line */
     LW_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
     LW_ERR_BUSY = 6,          /* the context is in use by another call */
     LW_ERR_CANCELLED = 7      /* a served request was cancelled before it ran */

@@ -274,6 +274,15 @@ lw_status enqueue(lw_ctx *ctx, float *ddist, long long n, int linkage, int32_t *
     p.merges = dmerges;
     p.heights = dheights;
     lw::bind_workspace(p, ws, L);
+    if (use_full) {
+        lw::check_range(p, p.D, nn);
+        lw::check_range(p, p.TL, nn);
+        lw::check_range(p, p.stamp, align256((size_t)n * sizeof(int)));
+    } else {
+        lw::check_range(p, p.D, (unsigned long long)n * (unsigned long long)(n - 1) / 2 * sizeof(float));
+    }
+    lw::check_range(p, p.merges, 8ull * (unsigned long long)(n - 1));
+    lw::check_range(p, p.heights, 4ull * (unsigned long long)(n - 1));
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = (unsigned long long)ctx->timeout_ms * 1000000ull;
     p.skip_arrive_cta = (ctx->test_skip_arrive >= 0 && ctx->test_skip_arrive < G && G > 1)
@@ -328,6 +337,11 @@ lw_status finish(lw_ctx *ctx)
     }
     if (st == lw::kErrInternal) {
         set_err(ctx, "kernel stopped: the decided pair was out of range (internal error)");
+        return LW_ERR_CUDA;
+    }
+    if (st == lw::kErrBounds) {
+        set_err(ctx, "bounds-checked build: an access outside the job's buffers (lw_merge.cu line %d)",
+                ctx->h_status[2]);
         return LW_ERR_CUDA;
     }
     if (st != 0) {

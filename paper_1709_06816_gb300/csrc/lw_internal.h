@@ -29,7 +29,17 @@ constexpr unsigned kRowStop = 0x80000000u;   // the row's cache ends here (cells
 constexpr unsigned kHardStop = 0x40000000u;  // the CTA published no entries beyond this one
 
 // Status words written by the kernel (values match lw_status).
-enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5 };
+enum : int { kOk = 0, kErrInput = 2, kErrInternal = 4, kErrTimeout = 5, kErrBounds = 6 };
+
+// Bounds-checked build (-DLW_CHECKED): every global load and store of the
+// merge kernel is checked against the job's buffers; one outside them is
+// skipped (a load reads zero) and sets the status to kErrBounds with the
+// source line in status[2].  For testing: it replaces a memory checker.
+constexpr int kCheckRanges = 8;
+struct CheckRange {
+    const char *base;
+    unsigned long long bytes;
+};
 
 // One CTA's record at the start of a round, 240 bytes: its smallest cache
 // entries (kPub of them, kPubOne for a one-CTA job; key = (bits(value) << 32)
@@ -76,7 +86,25 @@ struct MergeParams {
                                    // first barrier (-1 = off), so the others' bounded
                                    // wait runs out and reports LW_ERR_TIMEOUT
     int timing;                    // accumulate per-phase wall-clock time in stats[8..13]
+#ifdef LW_CHECKED
+    CheckRange ck[kCheckRanges];   // the job's buffers (checked build only)
+    int nck;
+#endif
 };
+
+// Registers [base, base + bytes) as a buffer the checked kernel may touch
+// (no effect in the normal build).
+__host__ __device__ inline void check_range(MergeParams &p, const void *base, unsigned long long bytes)
+{
+#ifdef LW_CHECKED
+    if (p.nck < kCheckRanges && base)
+        p.ck[p.nck++] = CheckRange{static_cast<const char *>(base), bytes};
+#else
+    (void)p;
+    (void)base;
+    (void)bytes;
+#endif
+}
 
 // Byte offsets of the merge kernel's global scratch inside one workspace
 // block (every part 256-byte aligned).  The words from `zero` to `total`
@@ -111,6 +139,10 @@ __host__ __device__ inline void bind_workspace(MergeParams &p, char *ws, const W
     p.parts = reinterpret_cast<unsigned long long *>(ws + L.parts);
     p.bar = reinterpret_cast<unsigned int *>(ws + L.bar);
     p.status = reinterpret_cast<int *>(ws + L.status);
+#ifdef LW_CHECKED
+    p.nck = 0;
+#endif
+    check_range(p, ws, L.total);
 }
 
 // One job of a batch (device table entry).

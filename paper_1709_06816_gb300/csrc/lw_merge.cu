@@ -78,6 +78,45 @@ namespace {
 typedef unsigned long long u64;
 constexpr int K = kCacheKeys;
 
+// Global loads and stores of the merge kernel: L2 only (see "Memory model"),
+// and in the bounds-checked build (-DLW_CHECKED) checked against the job's
+// buffers first (an address outside them is skipped, a load reads zero, and
+// the status records kErrBounds and the source line).
+#ifdef LW_CHECKED
+__device__ __noinline__ bool check_ok(const MergeParams &p, const void *a, unsigned bytes, int line)
+{
+    const char *c = static_cast<const char *>(a);
+    for (int q = 0; q < p.nck; ++q)
+        if (c >= p.ck[q].base && c + bytes <= p.ck[q].base + p.ck[q].bytes)
+            return true;
+    if (atomicCAS(p.status, 0, kErrBounds) == 0)
+        atomicExch(p.status + 2, line);
+    return false;
+}
+template <class T>
+struct same_type {
+    typedef T type;
+};
+template <class T>
+__device__ __forceinline__ T ld_checked(const MergeParams &p, const T *a, int line)
+{
+    return check_ok(p, a, sizeof(T), line) ? __ldcg(a) : T();
+}
+template <class T>
+__device__ __forceinline__ void st_checked(const MergeParams &p, T *a, typename same_type<T>::type v, int line)
+{
+    if (check_ok(p, a, sizeof(T), line))
+        __stcg(a, v);
+}
+#define LDCG(a) ld_checked(p, (a), __LINE__)
+#define STCG(a, v) st_checked(p, (a), (v), __LINE__)
+#define CHECKED_16(a) check_ok(p, (a), 16, __LINE__)
+#else
+#define LDCG(a) __ldcg(a)
+#define STCG(a, v) __stcg((a), (v))
+#define CHECKED_16(a) true
+#endif
+
 __device__ __forceinline__ long long tri_off(long long r, long long n)
 {
     return r * n - ((r * (r + 1)) >> 1);
@@ -102,8 +141,8 @@ __device__ __forceinline__ long long row_base(const MergeParams &p, long long r)
 __device__ __forceinline__ float member_cell(const MergeParams &p, long long x, int sx, long long y, int sy)
 {
     if (!p.full)
-        return __ldcg(p.D + pair_idx(x, y, p.n));
-    return sx >= sy ? __ldcg(p.D + x * p.pitch + y) : __ldcg(p.D + y * p.pitch + x);
+        return LDCG(p.D + pair_idx(x, y, p.n));
+    return sx >= sy ? LDCG(p.D + x * p.pitch + y) : LDCG(p.D + y * p.pitch + x);
 }
 
 __device__ __forceinline__ u64 make_key(float v, unsigned c)
@@ -513,7 +552,7 @@ __device__ __forceinline__ void init_cell(float v, long long q, unsigned c, cons
     unsigned u = __float_as_uint(v);
     if (u > 0x7f7fffffu) {
         if (u == 0x80000000u) {
-            __stcg(p.D + q, 0.0f);
+            STCG(p.D + q, 0.0f);
             u = 0u;
         } else {
             bad = 1;
@@ -546,16 +585,16 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
         a0 = end;
     const long long a1 = a0 + ((end - a0) & ~3LL);
     for (long long q = start + lane; q < a0; q += 32)
-        init_cell(__ldcg(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
+        init_cell(LDCG(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
     for (long long q = a1 + lane; q < end; q += 32)
-        init_cell(__ldcg(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
+        init_cell(LDCG(p.D + q), q, (unsigned)(q + base_c), p, L, bad);
     // 128-bit body, four loads in flight per lane
     long long q = a0 + 4 * lane;
     for (; q + 3 * 128 < a1; q += 4 * 128) {
         float4 x[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            x[u] = __ldcg(reinterpret_cast<const float4 *>(p.D + q + 128 * u));
+            x[u] = LDCG(reinterpret_cast<const float4 *>(p.D + q + 128 * u));
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const long long qq = q + 128 * u;
@@ -567,7 +606,7 @@ __device__ void warp_row_topk(const MergeParams &p, long long r, u64 (&out)[K], 
         }
     }
     for (; q < a1; q += 128) {
-        const float4 x = __ldcg(reinterpret_cast<const float4 *>(p.D + q));
+        const float4 x = LDCG(reinterpret_cast<const float4 *>(p.D + q));
         const unsigned c = (unsigned)(q + base_c);
         init_cell(x.x, q, c, p, L, bad);
         init_cell(x.y, q + 1, c + 1, p, L, bad);
@@ -613,9 +652,9 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
         a0 = end;
     const long long a1 = a0 + ((end - a0) & ~3LL);
     for (long long q = start + ts; q < a0; q += TB)
-        take(__ldcg(p.D + q), q);
+        take(LDCG(p.D + q), q);
     for (long long q = a1 + ts; q < end; q += TB)
-        take(__ldcg(p.D + q), q);
+        take(LDCG(p.D + q), q);
     const float4 *D4 = reinterpret_cast<const float4 *>(p.D);
     const long long j1 = a1 >> 2;
     for (long long j0 = (a0 >> 2) + ts; j0 < j1; j0 += 8 * TB) {
@@ -623,7 +662,7 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const long long j = j0 + (long long)u * TB;
-            v[u] = j < j1 ? __ldcg(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
+            v[u] = j < j1 ? LDCG(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -659,7 +698,7 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
     u64 tm0 = tlog && ts == 0 ? global_ns() : 0;
     const long long n = p.n;
     const long long nwords = (n + 31) / 32;
-    const int sr = __ldcg(p.stamp + r);
+    const int sr = LDCG(p.stamp + r);
     u64 L[K];
 #pragma unroll
     for (int q = 0; q < K; ++q)
@@ -687,8 +726,8 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
                 const long long q = q0 + (long long)u * TB;
                 c[u] = -1;
                 if (q < t1 && ((vpos[q >> 5] >> (q & 31)) & 1u)) {
-                    c[u] = q < t0 ? __ldcg(p.merges + 2 * q) : sh.pi[q - t0];
-                    v[u] = __ldcg(log + q);
+                    c[u] = q < t0 ? LDCG(p.merges + 2 * q) : sh.pi[q - t0];
+                    v[u] = LDCG(log + q);
                 }
             }
 #pragma unroll
@@ -721,10 +760,10 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
     const long long c_b = c_a + ((n - c_a) & ~3LL);
     for (long long c = r + 1 + ts; c < c_a; c += TB)
         if (cur(c))
-            take(__ldcg(row + c), c);
+            take(LDCG(row + c), c);
     for (long long c = c_b + ts; c < n; c += TB)
         if (cur(c))
-            take(__ldcg(row + c), c);
+            take(LDCG(row + c), c);
     {
         constexpr int U = 8;
         const float4 *R4 = reinterpret_cast<const float4 *>(row);
@@ -738,7 +777,7 @@ __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const long long j = j0 + (long long)u * TB;
-                v[u] = j < j1 ? __ldcg(R4 + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                v[u] = j < j1 ? LDCG(R4 + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
             if (first) {
                 u64 mn = kNoKey;
@@ -804,7 +843,7 @@ __device__ __noinline__ void block_row_topk_cols(const MergeParams &p, long long
     const int ts = threadIdx.x - (NT - TB);  // thread of the team
     const u64 tm0 = tlog && ts == 0 ? global_ns() : 0;
     const long long n = p.n;
-    const int sr = __ldcg(p.stamp + r);
+    const int sr = LDCG(p.stamp + r);
     const float *row = p.D + r * p.pitch;
     const float *log = p.TL + r * p.pitch;
     u64 L[K];
@@ -815,8 +854,8 @@ __device__ __noinline__ void block_row_topk_cols(const MergeParams &p, long long
     auto one = [&](long long c) {
         if (live(bitmap, c)) {
             ++cnt;
-            const int sc = __ldcg(p.stamp + c);
-            const float v = sc > sr ? __ldcg(log + sc) : __ldcg(row + c);
+            const int sc = LDCG(p.stamp + c);
+            const float v = sc > sr ? LDCG(log + sc) : LDCG(row + c);
             const u64 key = make_key(v, (unsigned)c);
             if (key < L[K - 1])
                 list_insert(L, key);
@@ -849,8 +888,8 @@ __device__ __noinline__ void block_row_topk_cols(const MergeParams &p, long long
                 const long long j = j0 + (long long)u * TB;
                 m4[u] = 0u;
                 if (j < j1) {
-                    const float4 a = __ldcg(R4 + j);
-                    const int4 b = __ldcg(S4 + j);
+                    const float4 a = LDCG(R4 + j);
+                    const int4 b = LDCG(S4 + j);
                     v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
                     sc[u][0] = b.x; sc[u][1] = b.y; sc[u][2] = b.z; sc[u][3] = b.w;
                     const long long c = j << 2;
@@ -862,7 +901,7 @@ __device__ __noinline__ void block_row_topk_cols(const MergeParams &p, long long
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (((m4[u] >> e) & 1u) && sc[u][e] > sr)
-                        v[u][e] = __ldcg(log + sc[u][e]);
+                        v[u][e] = LDCG(log + sc[u][e]);
             }
             if (first) {
                 u64 mn = kNoKey;
@@ -930,9 +969,9 @@ __device__ __noinline__ void warp_row_refresh(const MergeParams &p, long long r,
         a0 = end;
     const long long a1 = a0 + ((end - a0) & ~3LL);
     for (long long q = start + lane; q < a0; q += 32)
-        take(__ldcg(p.D + q), q);
+        take(LDCG(p.D + q), q);
     for (long long q = a1 + lane; q < end; q += 32)
-        take(__ldcg(p.D + q), q);
+        take(LDCG(p.D + q), q);
     const float4 *D4 = reinterpret_cast<const float4 *>(p.D);
     const long long j1 = a1 >> 2;
     for (long long j0 = (a0 >> 2) + lane; j0 < j1; j0 += 8 * 32) {
@@ -940,7 +979,7 @@ __device__ __noinline__ void warp_row_refresh(const MergeParams &p, long long r,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const long long j = j0 + 32 * u;
-            v[u] = j < j1 ? __ldcg(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
+            v[u] = j < j1 ? LDCG(D4 + j) : make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -1118,8 +1157,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (tid == PUB - 1)
                     col |= kHardStop;  // more entries may follow: none is published
             }
-            __stcg(&p.recA[b].key[tid], key);
-            __stcg(&p.recA[b].col[tid], col);
+            STCG(&p.recA[b].key[tid], key);
+            STCG(&p.recA[b].col[tid], col);
         }
         if (tid == 0) {
             const int par = (rr - 1) & 1;
@@ -1132,9 +1171,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             for (int q = 0; q < kReqPerCta; ++q)
                 rows[q] = q < nq ? (int)row_of(sh.myreq_l[par][q]) : -1;
             uint4 *dst = reinterpret_cast<uint4 *>(&p.recA[b].nreq);
-            __stcg(dst + 0, make_uint4((unsigned)nq, (unsigned)rows[0], (unsigned)rows[1], (unsigned)rows[2]));
-            __stcg(dst + 1, make_uint4((unsigned)rows[3], (unsigned)rows[4], (unsigned)rows[5], (unsigned)rows[6]));
-            __stcg(dst + 2, make_uint4((unsigned)rows[7], 0u, 0u, 0u));
+            STCG(dst + 0, make_uint4((unsigned)nq, (unsigned)rows[0], (unsigned)rows[1], (unsigned)rows[2]));
+            STCG(dst + 1, make_uint4((unsigned)rows[3], (unsigned)rows[4], (unsigned)rows[5], (unsigned)rows[6]));
+            STCG(dst + 2, make_uint4((unsigned)rows[7], 0u, 0u, 0u));
         }
     };
 
@@ -1152,9 +1191,9 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         mflag[l] = 0;
     }
     for (long long r = (long long)b * NT + tid; r < n; r += (long long)G * NT) {
-        p.size_g[r] = 1;
+        STCG(p.size_g + r, 1);
         if (p.full)
-            __stcg(p.stamp + r, -1);
+            STCG(p.stamp + r, -1);
     }
     if (tid == 0) {
         sh.ninst = 0;
@@ -1229,21 +1268,21 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 const ulonglong2 *ks = reinterpret_cast<const ulonglong2 *>(rec->key);
 #pragma unroll
                 for (int q = 0; q < PUB / 2; ++q) {
-                    const ulonglong2 kk = __ldcg(ks + q);
+                    const ulonglong2 kk = LDCG(ks + q);
                     wkey[tid * PUB + 2 * q] = kk.x;
                     wkey[tid * PUB + 2 * q + 1] = kk.y;
                 }
                 const uint4 *cs = reinterpret_cast<const uint4 *>(rec->col);
 #pragma unroll
                 for (int q = 0; q < PUB / 4; ++q) {
-                    const uint4 cc = __ldcg(cs + q);
+                    const uint4 cc = LDCG(cs + q);
                     wcol[tid * PUB + 4 * q] = cc.x;
                     wcol[tid * PUB + 4 * q + 1] = cc.y;
                     wcol[tid * PUB + 4 * q + 2] = cc.z;
                     wcol[tid * PUB + 4 * q + 3] = cc.w;
                 }
                 const uint4 *src = reinterpret_cast<const uint4 *>(&rec->nreq);
-                const uint4 w3 = __ldcg(src), w4 = __ldcg(src + 1), w5 = __ldcg(src + 2);
+                const uint4 w3 = LDCG(src), w4 = LDCG(src + 1), w5 = LDCG(src + 2);
                 rcnt = (int)w3.x;
                 rq[0] = (int)w3.y;
                 rq[1] = (int)w3.z;
@@ -1348,18 +1387,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                                 if (qa) {
                                     // (the arrays are padded to whole 16-byte words)
                                     int *w = sh.qw[np];
-                                    copy16_async(w, p.size_g + (row & ~3));
-                                    copy16_async(w + 4, p.size_g + (c & ~3));
-                                    if (p.full) {
+                                    if (CHECKED_16(p.size_g + (row & ~3)) && CHECKED_16(p.size_g + (c & ~3))) {
+                                        copy16_async(w, p.size_g + (row & ~3));
+                                        copy16_async(w + 4, p.size_g + (c & ~3));
+                                    }
+                                    if (p.full && CHECKED_16(p.stamp + (row & ~3)) && CHECKED_16(p.stamp + (c & ~3))) {
                                         copy16_async(w + 8, p.stamp + (row & ~3));
                                         copy16_async(w + 12, p.stamp + (c & ~3));
                                     }
                                 } else {
-                                    q_szi = __ldcg(p.size_g + row);
-                                    q_szj = __ldcg(p.size_g + c);
+                                    q_szi = LDCG(p.size_g + row);
+                                    q_szj = LDCG(p.size_g + c);
                                     if (p.full) {
-                                        q_si = __ldcg(p.stamp + row);
-                                        q_sj = __ldcg(p.stamp + c);
+                                        q_si = LDCG(p.stamp + row);
+                                        q_sj = LDCG(p.stamp + c);
                                     }
                                 }
                             }
@@ -1416,7 +1457,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         p.parts + ((size_t)ipar * kMaxReq + pos) * K);
 #pragma unroll
                     for (int q = 0; q < K / 2; ++q) {
-                        const ulonglong2 v = __ldcg(src + q);
+                        const ulonglong2 v = LDCG(src + q);
                         M[2 * q] = v.x;
                         M[2 * q + 1] = v.y;
                     }
@@ -1428,7 +1469,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (lane < np2) {
                     const long long ia = sh.ppi[lane];
                     if (ia > row)
-                        xr = make_key(__ldcg(p.full ? p.D + ia * p.pitch + row : p.D + base + ia), (unsigned)ia);
+                        xr = make_key(LDCG(p.full ? p.D + ia * p.pitch + row : p.D + base + ia), (unsigned)ia);
                 }
                 u64 xs[S];
 #pragma unroll
@@ -1492,7 +1533,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 if (tid - 32 < K / 2) {
                     const int h = tid - 32;
                     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(p.parts + ((size_t)par * kMaxReq + s2) * K);
-                    __stcg(dst + h, make_ulonglong2(sh.tko[2 * h], sh.tko[2 * h + 1]));
+                    STCG(dst + h, make_ulonglong2(sh.tko[2 * h], sh.tko[2 * h + 1]));
                 }
             }
             if (tid == 32)
@@ -1610,12 +1651,12 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                                 vb[u] = 0.0f;
                                 if (a < s) {
                                     if (full) {
-                                        va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
-                                        vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                                        va[u] = LDCG(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                        vb[u] = LDCG(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
                                     } else {
                                         const long long i = sh.pi[a], j = sh.pj[a];
-                                        va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
-                                        vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                        va[u] = LDCG(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                        vb[u] = LDCG(p.D + (k > j ? sh.bj[a] + k : bk + j));
                                     }
                                 }
                             }
@@ -1651,8 +1692,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                 mh = y < mh ? y : mh;
             }
             if (rpart == 0) {
-                __stcg(p.recB + (size_t)b * 2 * kRound + ra, ma);
-                __stcg(p.recB + (size_t)b * 2 * kRound + kRound + ra, mh);
+                STCG(p.recB + (size_t)b * 2 * kRound + ra, ma);
+                STCG(p.recB + (size_t)b * 2 * kRound + kRound + ra, mh);
             }
         } else if (s > 0) {
             for (int l0 = 0; l0 < R; l0 += NT) {
@@ -1686,11 +1727,11 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                         if (ok && a < s) {
                             const long long i = sh.pi[a], j = sh.pj[a];
                             if (full) {
-                                va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
-                                vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                                va[u] = LDCG(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                vb[u] = LDCG(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
                             } else {
-                                va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
-                                vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                va[u] = LDCG(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                vb[u] = LDCG(p.D + (k > j ? sh.bj[a] + k : bk + j));
                             }
                         }
                     }
@@ -1754,7 +1795,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     const u64 x = tid < S ? sh.wam[w][a] : sh.whm[w][a];
                     m = x < m ? x : m;
                 }
-                __stcg(p.recB + (size_t)b * 2 * kRound + (tid < S ? tid : kRound + tid - S), m);
+                STCG(p.recB + (size_t)b * 2 * kRound + (tid < S ? tid : kRound + tid - S), m);
             }
         }
         lap(ph2);
@@ -1798,8 +1839,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             u64 ma = kNoKey, mh = kNoKey;
             if (a < s) {
                 for (int g = tid / S; g < G; g += NT / S) {
-                    const u64 x = __ldcg(p.recB + (size_t)g * 2 * kRound + a);
-                    const u64 y = __ldcg(p.recB + (size_t)g * 2 * kRound + kRound + a);
+                    const u64 x = LDCG(p.recB + (size_t)g * 2 * kRound + a);
+                    const u64 y = LDCG(p.recB + (size_t)g * 2 * kRound + kRound + a);
                     ma = x < ma ? x : ma;
                     mh = y < mh ? y : mh;
                 }
@@ -1882,20 +1923,20 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         // ---- bookkeeping of the L merges
         if (b == 0) {
             if (tid < L) {
-                p.merges[2 * (t + tid)] = (int32_t)sh.pi[tid];
-                p.merges[2 * (t + tid) + 1] = (int32_t)sh.pj[tid];
-                p.heights[t + tid] = sh.ph[tid];
-                __stcg(p.size_g + sh.pi[tid], sh.szi[tid] + sh.szj[tid]);
+                STCG(p.merges + 2 * (t + tid), (int32_t)sh.pi[tid]);
+                STCG(p.merges + 2 * (t + tid) + 1, (int32_t)sh.pj[tid]);
+                STCG(p.heights + t + tid, sh.ph[tid]);
+                STCG(p.size_g + sh.pi[tid], sh.szi[tid] + sh.szj[tid]);
             }
             for (int e = tid; e < L * L; e += NT) {
                 const int a = e / L, c = e % L;
                 if (a < c) {
                     if (p.full) {
                         // merge c, the later one, rewrites row i_c; i_a's log at merge c
-                        __stcg(p.D + (long long)sh.pi[c] * p.pitch + sh.pi[a], sh.C[a][c]);
-                        __stcg(p.TL + (long long)sh.pi[a] * p.pitch + t + c, sh.C[a][c]);
+                        STCG(p.D + (long long)sh.pi[c] * p.pitch + sh.pi[a], sh.C[a][c]);
+                        STCG(p.TL + (long long)sh.pi[a] * p.pitch + t + c, sh.C[a][c]);
                     } else {
-                        __stcg(p.D + pair_idx(sh.pi[a], sh.pi[c], n), sh.C[a][c]);
+                        STCG(p.D + pair_idx(sh.pi[a], sh.pi[c], n), sh.C[a][c]);
                     }
                 }
             }
@@ -1910,7 +1951,7 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
             // row-log layout: merge t + tid rewrites row i (every CTA writes the
             // same value, so each one sees the new stamps in its own rescans)
             if (p.full) {
-                __stcg(p.stamp + sh.pi[tid], (int)(t + tid));
+                STCG(p.stamp + sh.pi[tid], (int)(t + tid));
                 // the members' earlier merges are no longer the latest; this one is
                 const int si = sh.si[tid], sj = sh.sj[tid];
                 if (si >= 0)
@@ -2037,10 +2078,10 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                     if (full) {
                         // row i_a is rewritten whole; row k keeps its stale copy
                         // and the new value goes to k's log at this merge
-                        __stcg(p.D + sh.bi[a] + k, v);
-                        __stcg(p.TL + bk + t + a, v);
+                        STCG(p.D + sh.bi[a] + k, v);
+                        STCG(p.TL + bk + t + a, v);
                     } else {
-                        __stcg(p.D + (k > ia ? sh.bi[a] + k : bk + ia), v);
+                        STCG(p.D + (k > ia ? sh.bi[a] + k : bk + ia), v);
                     }
                     ++st_updates;
                     if (k < ja) {
@@ -2087,12 +2128,12 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                                 vb[u] = 0.0f;
                                 if (a < L) {
                                     if (full) {
-                                        va[u] = __ldcg(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
-                                        vb[u] = __ldcg(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
+                                        va[u] = LDCG(sh.si[a] >= sk ? p.D + sh.bi[a] + k : p.TL + sh.bi[a] + sk);
+                                        vb[u] = LDCG(sh.sj[a] >= sk ? p.D + sh.bj[a] + k : p.TL + sh.bj[a] + sk);
                                     } else {
                                         const long long i = sh.pi[a], j = sh.pj[a];
-                                        va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
-                                        vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                        va[u] = LDCG(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                        vb[u] = LDCG(p.D + (k > j ? sh.bj[a] + k : bk + j));
                                     }
                                 }
                             }
@@ -2118,8 +2159,8 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
                             vb[u] = 0.0f;
                             if (!have && a < L) {
                                 const long long i = sh.pi[a], j = sh.pj[a];
-                                va[u] = __ldcg(p.D + (k > i ? sh.bi[a] + k : bk + i));
-                                vb[u] = __ldcg(p.D + (k > j ? sh.bj[a] + k : bk + j));
+                                va[u] = LDCG(p.D + (k > i ? sh.bi[a] + k : bk + i));
+                                vb[u] = LDCG(p.D + (k > j ? sh.bj[a] + k : bk + j));
                             }
                         }
 #pragma unroll
@@ -2311,6 +2352,9 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
         p.merges = J.merges;
         p.heights = J.heights;
         bind_workspace(p, ws, L);
+        check_range(p, J.D, (unsigned long long)J.n * (unsigned long long)(J.n - 1) / 2 * sizeof(float));
+        check_range(p, J.merges, 8ull * (unsigned long long)(J.n > 1 ? J.n - 1 : 0));
+        check_range(p, J.heights, 4ull * (unsigned long long)(J.n > 1 ? J.n - 1 : 0));
         p.stats = nullptr;
         p.timeout_ns = bp.timeout_ns;
         p.skip_arrive_cta = -1;
@@ -2323,7 +2367,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchParams bp)
             merge_job<NT, kPubOne>(p, 0, smem_raw, sh);
         __syncthreads();
         if (threadIdx.x == 0) {
-            bp.job_status[jb] = J.n > 1 ? __ldcg(p.status) : 0;
+            bp.job_status[jb] = J.n > 1 ? LDCG(p.status) : 0;
             merges_done += J.n > 1 ? J.n - 1 : 0;
         }
     }

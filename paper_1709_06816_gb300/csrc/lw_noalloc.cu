@@ -106,6 +106,9 @@ extern "C" lw_status lw_cluster_noalloc(float *dist, int64_t n, int linkage, int
     p.merges = merges_out;
     p.heights = heights_out;
     lw::bind_workspace(p, ws, L);
+    lw::check_range(p, dist, (unsigned long long)n * (unsigned long long)(n - 1) / 2 * sizeof(float));
+    lw::check_range(p, merges_out, 8ull * (unsigned long long)(n - 1));
+    lw::check_range(p, heights_out, 4ull * (unsigned long long)(n - 1));
     p.stats = reinterpret_cast<long long *>(ws + L.stats);
     p.timeout_ns = 5000ull * 1000000ull;
     p.skip_arrive_cta = -1;

@@ -17,6 +17,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblw.so")
+# built with -DLW_CHECKED (global accesses of the merge kernel bounds-checked);
+# loaded instead of liblw.so when LW_CHECKED=1 is in the environment
+CHECKED_LIB_PATH = os.path.join(_HERE, "liblw_checked.so")
 
 LW_SINGLE, LW_COMPLETE, LW_AVERAGE, LW_WARD, LW_WEIGHTED, LW_CENTROID = 0, 1, 2, 3, 4, 5
 LINKAGES = {"single": 0, "complete": 1, "average": 2, "ward": 3, "weighted": 4, "centroid": 5}
@@ -65,9 +68,12 @@ class LwError(RuntimeError):
         super().__init__(f"{STATUS.get(status, status)}: {detail}")
 
 
-def load(path: str = LIB_PATH):
-    """Load liblw.so (raises if it is not built)."""
+def load(path: str | None = None):
+    """Load liblw.so, or liblw_checked.so when LW_CHECKED=1 (raises if it is
+    not built)."""
     global _lib
+    if path is None:
+        path = CHECKED_LIB_PATH if os.environ.get("LW_CHECKED") == "1" else LIB_PATH
     with _lock:
         if _lib is not None:
             return _lib
