@@ -516,17 +516,21 @@ def run_other_configs(args, local, peak):
         work = torch.empty_like(src)
         m_out = torch.empty((n - 1, 2), dtype=torch.int32, device=dev)
         h_out = torch.empty(n - 1, dtype=torch.float32, device=dev)
+        D_host = src.cpu().numpy() if not args.no_cpu_baseline else None
         for link in (0, 1, 2):
             km, _ = time_steps(ctx, stream, src, work, n, link, m_out, h_out, 2, 5)
             k = sum(km) / len(km)
-            alg, note = algorithmic_bytes(n, link, work_counts(f"gmm16384q:{link}"))
+            rec = work_counts(f"gmm16384q:{link}")
+            alg, note = algorithmic_bytes(n, link, rec)
             out[f"gmm16384q_{LINK_NAMES[link]}"] = {
                 "n": n, "linkage": LINK_NAMES[link], "dendrogram_ms": k, "merges_per_s": (n - 1) / (k * 1e-3),
                 "roofline": {"bound": "hbm", "achieved": alg / (k * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": alg / (k * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
                              "algorithmic_note": note},
                 "parity": parity_block(m_out.cpu().numpy(), h_out.cpu().numpy(), f"gmm16384q:{link}")}
-        del src, work
+            if D_host is not None:
+                out[f"gmm16384q_{LINK_NAMES[link]}"]["cpu"] = cpu_single_and_all(D_host, n, link, rec)
+        del src, work, D_host
         torch.cuda.empty_cache()
 
         w = synth.workload("gmm512")
@@ -538,7 +542,15 @@ def run_other_configs(args, local, peak):
         h_out = torch.empty(n - 1, dtype=torch.float32, device=dev)
         km, _ = time_steps(ctx, stream, src, work, n, 1, m_out, h_out, 5, 50)
         k = sum(km) / len(km)
+        cores = oracle.threads()
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.cached(D, n, 1)
+        one_s = time.perf_counter() - t0
+        oracle.set_threads(cores)
+        t0 = time.perf_counter()
         wm, wh, st, _ = oracle.cached(D, n, 1)
+        all_s = time.perf_counter() - t0
         same = bool(np.array_equal(m_out.cpu().numpy(), wm)
                     and np.array_equal(h_out.cpu().numpy().view(np.uint32), wh.view(np.uint32)))
         alg, _ = algorithmic_bytes(n, 1, st)
@@ -549,9 +561,33 @@ def run_other_configs(args, local, peak):
                          "frac": alg / (k * 1e-3) / 1e9 / l2, "algorithmic_bytes_per_launch": alg,
                          "peak_source": "measured here: L2-resident device copy (read + write bytes)",
                          "note": "one CTA (n <= 4096): a single SM works through 511 dependent merges"},
-            "parity": {"oracle_match": same, "reference": "oracle run here on the same matrix"}}
+            "parity": {"oracle_match": same, "reference": "oracle run here on the same matrix"},
+            "cpu": {"kind": "oracle, full runs on the same matrix", "single_thread_merges_per_s": (n - 1) / one_s,
+                    "all_cores_merges_per_s": (n - 1) / all_s, "cores": cores}}
     finally:
         ctx.close()
+    return out
+
+
+def cpu_single_and_all(D_host, n: int, link: int, rec) -> dict:
+    """The oracle on one host thread (a bounded sample of the same matrix, its
+    full-run time estimated by the work sum(m_t), uncalibrated) and on all of
+    them (the full run that made the stored digest)."""
+    import oracle
+    cores = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        smp = oracle.sample(D_host, n, link, target_s=3.0)
+    finally:
+        oracle.set_threads(cores)
+    out = {"kind": "oracle", "single_thread_merges_per_s": (n - 1) / smp["est_total_s"],
+           "single_thread_sample": f"validation + first {smp['K']} of {n - 1} merges on 1 thread "
+                                   f"({smp['wall_s']:.1f} s), full run estimated by the work sum(m_t), uncalibrated "
+                                   f"(on the n = 65536 matrix that model ran about 1.5x short of a full run)"}
+    if rec and rec.get("oracle_seconds"):
+        out["all_cores_merges_per_s"] = (n - 1) / rec["oracle_seconds"]
+        out["all_cores_note"] = (f"the full oracle run behind the stored digest, "
+                                 f"{rec.get('oracle_threads')} threads, {rec['oracle_seconds']} s")
     return out
 
 
