@@ -686,7 +686,10 @@ __device__ __noinline__ void block_row_topk(const MergeParams &p, long long r, c
 // in the scratch bitmap `newer`, part (b) skips them; only c > r count.
 // Merges t0 .. t0 + L0 - 1 (the current round, L0 > 0 only after this CTA's
 // own pass 2) take their survivors from the round's chain in shared memory,
-// older ones from the merge list.  Result in sh.tko.
+// older ones from the merge list.  Used by the owner's immediate rescans,
+// which run in the round they are needed (refill scans, which read the state
+// a whole round left, go column by column: block_row_topk_cols).  Result in
+// sh.tko.
 template <int NT, int S, int TB = NT>
 __device__ __noinline__ void block_row_topk_log(const MergeParams &p, long long r, const unsigned *bitmap,
                                    const unsigned *vpos, unsigned *newer, Shared<NT, S> &sh, long long t0,
