@@ -377,7 +377,7 @@ struct Shared {
     u64 gamin[S], ghmin[S];      // the same over all CTAs
     // (rows padded by one word: the certification reads a column of these
     // per warp, one row per lane, which would otherwise hit a single bank)
-    float Dm[2 * S][2 * S + 1];  // D between members (2a = i_a, 2a + 1 = j_a)
+    alignas(16) float Dm[2 * S][2 * S + 1];  // D between members (2a = i_a, 2a + 1 = j_a)
     float X[S][S + 1];           // cell (i_a, i_b) after merge a alone
     float Y[S][S + 1];           // cell (i_a, j_b) after merge a alone
     float C[S][S + 1];           // cell (i_a, i_b) after merges a then b (a < b)
@@ -1876,35 +1876,73 @@ __device__ void merge_job(const MergeParams &p, const int b, unsigned char *smem
         }
         __syncthreads();
         lap(xs3);
-        // certification: thread (p, a) takes the smallest cell that merge a
-        // (a < p) rewrote as seen after merge p - 1; the S threads of p reduce
-        // and compare with P_p
-        for (int e = tid; e < S * S; e += NT) {
-            const int pp = e / S, a = e % S;
-            Cand M = {kNoKey, 0xffffffffu};
-            if (pp >= 1 && pp < s && a < pp) {
-                const unsigned ia = (unsigned)sh.pi[a];
-                const u64 g = sh.gamin[a];
-                if (g != kNoKey)
-                    cand_min(M, cell_cand((unsigned)(g >> 32), ia, (unsigned)g));
-                for (int c = pp; c < s; ++c) {
-                    cand_min(M, cell_cand(__float_as_uint(sh.X[a][c]), ia, (unsigned)sh.pi[c]));
-                    cand_min(M, cell_cand(__float_as_uint(sh.Y[a][c]), ia, (unsigned)sh.pj[c]));
+        // certification: P_p is accepted when it is smaller than every cell
+        // that merges a < p rewrote, as seen after merge p - 1: for merge a,
+        // its published minimum over the other rows, the cells (i_a, i_c) and
+        // (i_a, j_c) after merge a alone for the pairs c >= p not merged yet,
+        // and (i_a, i_c) after merges a and c for a < c < p.  Warp per row a,
+        // lane c: the first term by a suffix minimum over the lanes, the second
+        // by an exclusive prefix minimum, so candidate R(a, p) sits in lane p;
+        // then warp per p, lane a: the minimum over a < p.  (R is kept in the
+        // member-cell table, whose values the round no longer needs.)
+        {
+            static_assert(sizeof(float) * 2 * S * (2 * S + 1) >= 12 * S * S, "candidates fit the member-cell table");
+            u64 *RA = reinterpret_cast<u64 *>(&sh.Dm[0][0]);
+            unsigned *Rc = reinterpret_cast<unsigned *>(RA + S * S);
+            const Cand none = {kNoKey, 0xffffffffu};
+            for (int a = warp; a + 1 < s; a += W) {  // (row s - 1 rewrites nothing a later p sees)
+                const int c = lane;
+                const bool in = c > a && c < s;
+                Cand xy = none, cc = none;
+                if (in) {
+                    const unsigned ia = (unsigned)sh.pi[a];
+                    xy = cell_cand(__float_as_uint(sh.X[a][c]), ia, (unsigned)sh.pi[c]);
+                    cand_min(xy, cell_cand(__float_as_uint(sh.Y[a][c]), ia, (unsigned)sh.pj[c]));
+                    cc = cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]);
                 }
-                for (int c = a + 1; c < pp; ++c)
-                    cand_min(M, cell_cand(__float_as_uint(sh.C[a][c]), ia, (unsigned)sh.pi[c]));
-            }
 #pragma unroll
-            for (int o = S / 2; o > 0; o >>= 1) {
-                Cand y;
-                y.A = __shfl_xor_sync(kFull, M.A, o);
-                y.c = __shfl_xor_sync(kFull, M.c, o);
-                cand_min(M, y);
+                for (int d = 1; d < 32; d <<= 1) {
+                    Cand y, z;
+                    y.A = __shfl_down_sync(kFull, xy.A, d);
+                    y.c = __shfl_down_sync(kFull, xy.c, d);
+                    z.A = __shfl_up_sync(kFull, cc.A, d);
+                    z.c = __shfl_up_sync(kFull, cc.c, d);
+                    if (lane + d < 32)
+                        cand_min(xy, y);
+                    if (lane >= d)
+                        cand_min(cc, z);
+                }
+                Cand e;
+                e.A = __shfl_up_sync(kFull, cc.A, 1);
+                e.c = __shfl_up_sync(kFull, cc.c, 1);
+                if (in) {
+                    cand_min(xy, lane >= 1 ? e : none);
+                    const u64 g = sh.gamin[a];
+                    if (g != kNoKey)
+                        cand_min(xy, cell_cand((unsigned)(g >> 32), (unsigned)sh.pi[a], (unsigned)g));
+                    RA[a * S + c] = xy.A;
+                    Rc[a * S + c] = xy.c;
+                }
             }
-            if (a == 0 && pp >= 1 && pp < s) {
-                const u64 PA = ((u64)__float_as_uint(sh.ph[pp]) << 32) | (unsigned)sh.pi[pp];
-                const unsigned Pc = (unsigned)sh.pj[pp];
-                sh.okp[pp] = PA < M.A || (PA == M.A && Pc < M.c);
+            __syncthreads();
+            for (int pp = 1 + warp; pp < s; pp += W) {
+                Cand M = none;
+                if (lane < pp) {
+                    M.A = RA[lane * S + pp];
+                    M.c = Rc[lane * S + pp];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    Cand y;
+                    y.A = __shfl_xor_sync(kFull, M.A, o);
+                    y.c = __shfl_xor_sync(kFull, M.c, o);
+                    cand_min(M, y);
+                }
+                if (lane == 0) {
+                    const u64 PA = ((u64)__float_as_uint(sh.ph[pp]) << 32) | (unsigned)sh.pi[pp];
+                    const unsigned Pc = (unsigned)sh.pj[pp];
+                    sh.okp[pp] = PA < M.A || (PA == M.A && Pc < M.c);
+                }
             }
         }
         __syncthreads();
