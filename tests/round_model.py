@@ -65,8 +65,13 @@ def lw_cell(linkage, dki, dkj, dij, ni, nj, nk):
 
 
 class RoundModel:
-    def __init__(self, packed, n, linkage, G=1, chain=16, pub=4, certify=True, refill_at=0):
+    def __init__(self, packed, n, linkage, G=1, chain=16, pub=4, certify=True, refill_at=0, scan=False):
         self.n, self.link, self.G = n, linkage, G
+        # scan: certify as the kernel does (per merge a, a suffix minimum over
+        # the pairs c >= p and an exclusive prefix minimum over a < c < p),
+        # instead of the direct loops over (p, a, c)
+        self.scan = scan
+        self.decisions = []
         self.refill_at = refill_at
         self.chain = chain
         self.pub = pub
@@ -196,7 +201,28 @@ class RoundModel:
                     C[a, c] = lw_cell(self.link, X[a, c], Y[a, c], chain[c][2], szi[c], szj[c], szi[a] + szj[a])
             # certification: P_{p+1} below every cell merges 0..p rewrote
             L = s
-            if self.certify:
+            if self.certify and self.scan:
+                def cell(vb, x, y):
+                    return (vb, min(x, y), max(x, y))
+                none = (1 << 40, 0, 0)
+                R = {}
+                for a in range(s - 1):
+                    ia = chain[a][0]
+                    suf = [none] * (s + 1)
+                    for c in range(s - 1, a, -1):
+                        suf[c] = min(suf[c + 1], cell(_bits(X[a, c]), ia, chain[c][0]),
+                                     cell(_bits(Y[a, c]), ia, chain[c][1]))
+                    g = cell(amin[a] >> 32, ia, amin[a] & 0xFFFFFFFF) if amin[a] != NOKEY else none
+                    pre = none
+                    for c in range(a + 1, s):
+                        R[a, c] = min(g, suf[c], pre)
+                        pre = min(pre, cell(_bits(C[a, c]), ia, chain[c][0]))
+                for pp in range(1, s):
+                    P = (_bits(chain[pp][2]), chain[pp][0], chain[pp][1])
+                    if not P < min(R[a, pp] for a in range(pp)):
+                        L = pp
+                        break
+            elif self.certify:
                 def cell(vb, x, y):
                     return (vb, min(x, y), max(x, y))
                 for pp in range(1, s):
@@ -214,6 +240,7 @@ class RoundModel:
                     if not P < low:
                         L = pp
                         break
+            self.decisions.append((s, L))
             # bookkeeping of the L merges
             for a in range(L):
                 merges.append((chain[a][0], chain[a][1]))

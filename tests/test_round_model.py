@@ -58,3 +58,22 @@ def test_uncertified_chain_is_caught():
             caught += 1
     assert caught > 0
 
+
+
+@pytest.mark.parametrize("link", [0, 1, 3])
+def test_certification_by_scans_decides_the_same(link):
+    """The kernel's form of the certification (per merge a, a suffix minimum
+    over the later pairs of the cells merge a alone wrote and an exclusive
+    prefix minimum over a < c < p of the cells after merges a and c) accepts
+    exactly the prefix the direct loops accept, round by round, ties
+    included."""
+    for s_, n in enumerate((40, 90)):
+        for D in (synth.tie_heavy(n, 300 + s_, levels=3), synth.small_gmm(n, 310 + s_)):
+            direct = RoundModel(D.copy(), n, link, G=3, chain=32, pub=4, refill_at=2)
+            scans = RoundModel(D.copy(), n, link, G=3, chain=32, pub=4, refill_at=2, scan=True)
+            m1, h1, _ = direct.run()
+            m2, h2, _ = scans.run()
+            assert direct.decisions == scans.decisions
+            assert np.array_equal(m1, m2) and np.array_equal(_bits(h1), _bits(h2))
+            wm, wh, _, _ = oracle.cached(D.copy(), n, link)
+            assert np.array_equal(m2, wm) and np.array_equal(_bits(h2), _bits(wh))
