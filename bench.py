@@ -456,7 +456,7 @@ def run_ours(args, world, rank, local):
     achieved = alg / (k_avg_ms * 1e-3) / 1e9
     clocks = clk.summary()
     out = {
-        "metric": METRIC,
+        "metric": METRIC if n == 65536 else METRIC.replace("n=65536", f"n={n}"),
         "value": world * args.steps * (n - 1) / (total_ms_max * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
